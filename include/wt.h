@@ -1,0 +1,235 @@
+/*
+ * wt.h -- C ABI of the GB300 (sm_103a) builder and query engine for the
+ * pointerless, level-wise wavelet tree of "Parallel Construction of Wavelet
+ * Trees on Multicore Architectures" (arXiv 1610.05994).
+ *
+ * The problem (Section 2.3): given S[0..n) over the alphabet [0, sigma),
+ * build the wavelet tree with one pointer per level (Section 2.2, Fig. 2b):
+ * L = ceil(lg sigma) bitmaps of n bits, level l holding the level-l bit of
+ * every symbol with the symbols ordered stably by their top l bits
+ * (Proposition 1), plus rank/select directories, and answer access, rank and
+ * select (Section 2.2).
+ *
+ * Conventions shared by every call:
+ *   - Symbols are codes in [0, sigma), stored as unsigned integers of
+ *     sym_width bytes (1, 2 or 4), little-endian, packed.
+ *   - Level l of node v holds the symbols s with s >> (L - l) == v; a node
+ *     splits on the bit (s >> (L - 1 - l)) & 1, so for sigma not a power of
+ *     two some nodes are empty.
+ *   - rank_c(i) counts c in the half-open prefix [0, i); select_c(j) is the
+ *     0-based position of the j-th (1-based) occurrence of c.
+ *   - Pointers named "device" must point to device memory of the current
+ *     CUDA device; S of a build may be device or host memory.
+ *   - A stream argument is a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream.  Calls that take a stream are asynchronous on
+ *     it unless stated.
+ *   - Functions returning wt_status also set the calling thread's last
+ *     status (wt_last_status()); functions returning a handle return NULL on
+ *     failure and set it.
+ *
+ * Serialised layout of one level (identical to what the CPU oracle emits):
+ *   words: ceil(n/512) * 16 uint32 words; bit p is bit (p & 31) of word
+ *          p >> 5 (equivalently byte p >> 3, bit p & 7); bits >= n are 0.
+ *   R:     ceil(n/512) + 1 uint32; R[b] = (ones in [0, 512 b)) mod 2^32.
+ *   Hy:    ceil(n/2^32) + 1 uint64; Hy[h] = ones in [0, min(n, 2^32 h)).
+ *   S1:    ceil(ones/8192) uint32; S1[k] = (position of the one of 0-based
+ *          rank 8192 k) >> 9.  S0: the same for zeros at positions < n.
+ *   ones:  ones in [0, n).
+ */
+#ifndef WT_H
+#define WT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque tree handle; owned by the library until wt_free. */
+typedef struct wt_tree *wt_handle;
+
+typedef enum {
+    WT_OK = 0,
+    WT_ERR_ARG = 1,          /* invalid argument (width, sigma, pointer, level) */
+    WT_ERR_SYMBOL_RANGE = 2, /* some S[j] >= sigma; found on the device, no trap */
+    WT_ERR_OOM = 3,          /* the allocator returned NULL */
+    WT_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    WT_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up */
+} wt_status;
+
+/* Construction variants.  AUTO picks per (n, sigma, width) from a measured
+ * table; LEVELWISE is the per-level pass (kernels a + b + c); DD builds every
+ * level straight from S with per-tile prefix histograms (kernel d, for small
+ * sigma only: it returns WT_ERR_ARG when 2^L - 1 node counters per tile do
+ * not fit). */
+typedef enum { WT_VARIANT_AUTO = 0, WT_VARIANT_LEVELWISE = 1, WT_VARIANT_DD = 2 } wt_variant;
+
+/* Query operation codes for wt_query_multi. */
+typedef enum { WT_OP_ACCESS = 0, WT_OP_RANK = 1, WT_OP_SELECT = 2 } wt_op;
+
+/* Largest supported alphabet: 2^28 codes (28 levels; the node tables take
+ * 3 * 2^L * 8 bytes during a build). */
+#define WT_MAX_SIGMA (1ull << 28)
+#define WT_MAX_LEVELS 28
+
+/*
+ * Builds the tree of S[0..n) over [0, sigma) (Section 2.3; Algorithm 1 is
+ * the sequential statement of what is built).  Synchronous: returns once the
+ * tree is resident and checked.  NULL on failure: WT_ERR_ARG for
+ * sym_width not in {1, 2, 4}, sigma == 0, sigma > 2^(8 sym_width) or
+ * sigma > WT_MAX_SIGMA, or S == NULL with n > 0; WT_ERR_SYMBOL_RANGE if any
+ * symbol is >= sigma; WT_ERR_OOM, WT_ERR_CUDA, WT_ERR_TIMEOUT otherwise.
+ * S may be host or device memory; the caller keeps ownership.
+ */
+wt_handle wt_build(const void *S, uint64_t n, uint64_t sigma, int sym_width);
+
+/*
+ * As wt_build, but enqueued on stream and returning at once; the handle is
+ * valid immediately for further calls on the same stream.  Arguments are
+ * checked on the host; device-side faults (symbol range, timeout) are
+ * reported by wt_wait.  S must stay valid until the build completes.
+ * variant is a wt_variant.
+ */
+wt_handle wt_build_async(const void *S, uint64_t n, uint64_t sigma, int sym_width, int variant,
+                         void *stream);
+
+/* Waits for a handle's build to finish and returns its device-reported status. */
+wt_status wt_wait(wt_handle h);
+
+/*
+ * Builds count trees in one batched, graph-launched pass (the sequences may
+ * differ in n, sigma and width).  S[k] are device pointers.  out[k] receives
+ * each handle (NULL on argument errors, then the call returns the first
+ * error).  Asynchronous on stream; wt_wait on any handle returns the batch's
+ * status.
+ */
+wt_status wt_build_batch(const void *const *S, const uint64_t *n, const uint64_t *sigma,
+                         const int *sym_width, uint32_t count, wt_handle *out, void *stream);
+
+/*
+ * access(i) for m device positions i[k] -> out[k] (device, uint32) by the
+ * top-down walk of Section 2.2 simulated with rank on the level bitmaps.
+ * i[k] >= n gives UINT32_MAX.
+ */
+wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, void *stream);
+
+/* rank_c(i) = occurrences of c[k] in [0, i[k]) -> out[k] (device arrays).
+ * c >= sigma or i > n gives UINT64_MAX. */
+wt_status wt_rank(wt_handle h, const uint32_t *c, const uint64_t *i, uint64_t m, uint64_t *out,
+                  void *stream);
+
+/* select_c(j) = 0-based position of the j[k]-th occurrence of c[k] -> out[k]
+ * (device arrays).  c >= sigma, j == 0 or j > count gives UINT64_MAX. */
+wt_status wt_select(wt_handle h, const uint32_t *c, const uint64_t *j, uint64_t m, uint64_t *out,
+                    void *stream);
+
+/*
+ * Mixed queries over several resident trees (the serving path): query k runs
+ * op[k] (a wt_op) on trees[tree_idx[k]] with symbol c[k] and argument arg[k]
+ * (i for access and rank, j for select); out[k] is the answer widened to
+ * uint64 (access sentinel UINT32_MAX becomes UINT64_MAX).  trees is a host
+ * array of ntrees handles; the other arrays are device arrays of length m.
+ */
+wt_status wt_query_multi(const wt_handle *trees, uint32_t ntrees, const uint32_t *tree_idx,
+                         const uint8_t *op, const uint32_t *c, const uint64_t *arg, uint64_t m,
+                         uint64_t *out, void *stream);
+
+/* Releases a handle.  The device memory is freed in stream order on the
+ * stream the tree was built on, without a host wait; work on other streams
+ * that still reads the tree must be complete (or ordered before) first. */
+wt_status wt_free(wt_handle h);
+
+typedef struct {
+    uint64_t n;
+    uint64_t sigma;
+    uint32_t levels;      /* L */
+    int32_t sym_width;
+    int32_t variant;      /* the wt_variant that built it */
+    int32_t reserved;
+    uint64_t device_bytes; /* resident bytes of the tree */
+} wt_info_t;
+
+/* Shape of a built tree; waits for the build. */
+wt_status wt_info(wt_handle h, wt_info_t *out);
+
+typedef struct {
+    const uint32_t *words;  /* device */
+    const uint32_t *R;      /* device */
+    const uint64_t *Hy;     /* device */
+    const uint32_t *S1;     /* device */
+    const uint32_t *S0;     /* device */
+    uint64_t ones;
+    uint64_t n_words, n_R, n_Hy, n_S1, n_S0;
+} wt_level_view_t;
+
+/* Device pointers and sizes of level l (layout above); waits for the build.
+ * The pointers stay valid until wt_free. */
+wt_status wt_level_view(wt_handle h, uint32_t l, wt_level_view_t *out);
+
+/*
+ * Routes every device allocation of the library through alloc/free_ (for
+ * example a framework's caching allocator).  alloc(bytes, stream, ctx) must
+ * return device memory usable in stream order on stream (or NULL);
+ * free_(ptr, bytes, stream, ctx) releases it in stream order.  Passing NULL
+ * for both restores cudaMallocAsync / cudaFreeAsync.
+ */
+wt_status wt_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
+                           void (*free_)(void *ptr, size_t bytes, void *stream, void *ctx), void *ctx);
+
+/* Last status set by a call of this thread. */
+wt_status wt_last_status(void);
+
+/* Static text for a status. */
+const char *wt_status_string(wt_status s);
+
+/*
+ * Stage entry points: one step of the build each, for tests and tooling.
+ *
+ * wt_node_starts (Algorithm 1 "count" and parPrefixSum, read as exclusive):
+ * Hex[c] = number of symbols < c, for c = 0 .. 2^L (entries at c >= sigma
+ * equal n), written to the device array Hex (2^L + 1 uint64).  The start of
+ * node v on level l is Hex[v << (L - l)].  S is a device pointer.  Returns
+ * WT_ERR_SYMBOL_RANGE (after a stream synchronisation) if a symbol is out of
+ * range.
+ */
+wt_status wt_node_starts(const void *S, uint64_t n, uint64_t sigma, int sym_width, uint64_t *Hex,
+                         void *stream);
+
+/*
+ * wt_level_step (the bit pass of Algorithm 1 for one level, plus the stable
+ * placement that yields the next level's order): given cur = P_l (the
+ * level-l order, device, n symbols) and Hex from wt_node_starts, writes the
+ * level-l bitmap to words (device, ceil(n/512) * 16 uint32), its block
+ * directory to R (device, ceil(n/512) + 1 uint32) and, when nxt is not NULL
+ * and l < L - 1, the order P_{l+1} to nxt (device, n symbols).  Synchronous
+ * (it waits for its stream).
+ */
+wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_width, uint32_t l,
+                        const uint64_t *Hex, uint32_t *words, uint32_t *R, void *nxt, void *stream);
+
+/*
+ * Per-kernel timing (no counterpart in the paper; it times the hot path).
+ * Between wt_profile_begin and wt_profile_end every kernel launch of the
+ * library is bracketed by CUDA events on the stream it runs on.
+ * wt_profile_end waits for those events and writes one record per kernel
+ * that ran (up to cap records to out; *count receives how many kernels
+ * ran): launches, summed device time and summed algorithmic bytes (the
+ * bytes the method must move for that launch: symbols read, bitmap and
+ * directory written, next-level order written).
+ */
+typedef struct {
+    char name[24];
+    uint64_t launches;
+    double total_ms;
+    double alg_bytes;
+} wt_kernel_stat_t;
+
+wt_status wt_profile_begin(void);
+wt_status wt_profile_end(wt_kernel_stat_t *out, uint32_t cap, uint32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WT_H */

@@ -56,8 +56,9 @@ def _load():
         lib.wto_select.argtypes = [vp, u64, u64, vp, vp, u64, vp]
         lib.wto_level_symbol.argtypes = [vp, u64, i32, u64, u32, u64, vp]
         lib.wto_access_trace.argtypes = [vp, u64, u64, u64, vp, vp]
+        lib.wto_node_starts.argtypes = [vp, u64, i32, u64, vp]
         for f in ("wto_level_order", "wto_build_bits", "wto_pwt", "wto_dd", "wto_directory",
-                  "wto_access", "wto_rank", "wto_select", "wto_level_symbol", "wto_access_trace"):
+                  "wto_access", "wto_rank", "wto_select", "wto_level_symbol", "wto_access_trace", "wto_node_starts"):
             getattr(lib, f).restype = i32
         _lib = lib
     return _lib
@@ -94,6 +95,14 @@ def level_order(S: np.ndarray, sigma: int, l: int) -> np.ndarray:
     S, w = _seq(S)
     out = np.empty(len(S), dtype=np.uint32)
     _check(_load().wto_level_order(_ptr(S), len(S), w, sigma, l, _ptr(out)))
+    return out
+
+
+def node_starts(S: np.ndarray, sigma: int) -> np.ndarray:
+    """Hex[c] = symbols below c, c = 0 .. 2^L (node v of level l starts at Hex[v << (L-l)])."""
+    S, w = _seq(S)
+    out = np.zeros((1 << levels(sigma)) + 1, dtype=np.uint64)
+    _check(_load().wto_node_starts(_ptr(S), len(S), w, sigma, _ptr(out)))
     return out
 
 

@@ -188,6 +188,31 @@ int wto_build_bits(const void *S, uint64_t n, int w, uint64_t sigma, uint8_t *bi
 }
 
 /*
+ * Node starts of every level at once: Hex[c] = number of symbols of S below
+ * c, for c = 0 .. 2^L (Algorithm 1's "count" step done once on the leaves,
+ * then its prefix sum, read as exclusive).  Node v of level l starts at
+ * Hex[v << (L - l)] because the node holds exactly the codes
+ * [v << (L - l), (v + 1) << (L - l)) (Proposition 1).  out holds 2^L + 1.
+ */
+int wto_node_starts(const void *S, uint64_t n, int w, uint64_t sigma, uint64_t *out)
+{
+    uint32_t *x = NULL;
+    int st = load_codes(S, n, w, sigma, &x);
+    if (st) return st;
+    uint32_t L = wto_levels(sigma);
+    uint64_t leaves = 1ull << L;
+    uint64_t *H = (uint64_t *)calloc(leaves, sizeof(uint64_t));
+    if (!H) { free(x); return WTO_ERR_NOMEM; }
+    for (uint64_t j = 0; j < n; j++) H[x[j]]++;
+    uint64_t run = 0;
+    for (uint64_t c = 0; c < leaves; c++) { out[c] = run; run += H[c]; }
+    out[leaves] = run;
+    free(H);
+    free(x);
+    return WTO_OK;
+}
+
+/*
  * Algorithm 1 (pwt) taken literally, run sequentially: for each level i,
  * count the symbols of every node (lines 5-6), take the exclusive prefix sum
  * as node offsets (line 7, reading R4), then scan S once more and set the bit

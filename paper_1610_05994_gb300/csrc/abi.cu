@@ -1,0 +1,699 @@
+// abi.cu -- the C ABI of include/wt.h: argument checks, device memory,
+// the build driver (which kernels run in which order) and query dispatch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "wt_internal.cuh"
+
+using namespace wt;
+
+namespace {
+
+thread_local wt_status g_last = WT_OK;
+
+struct Allocator {
+    void *(*alloc)(size_t, void *, void *);
+    void (*free_)(void *, size_t, void *, void *);
+    void *ctx;
+};
+Allocator g_alloc = {nullptr, nullptr, nullptr};
+std::mutex g_alloc_mu;
+
+wt_status set_last(wt_status s) {
+    g_last = s;
+    return s;
+}
+
+Allocator current_allocator() {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_alloc;
+}
+
+void *dev_alloc(const Allocator &A, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) bytes = 256;
+    if (A.alloc) return A.alloc(bytes, st, A.ctx);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(const Allocator &A, void *p, size_t bytes, cudaStream_t st) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    if (A.free_)
+        A.free_(p, bytes, st, A.ctx);
+    else
+        cudaFreeAsync(p, st);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------- profiler
+// While enabled, every kernel launch of the library is bracketed by two CUDA
+// events on its own stream and tagged with the launch's algorithmic bytes
+// (what the method must move: reads of the symbols, writes of bitmaps,
+// directories and the next level's order).  wt_profile_end reduces them per
+// kernel.
+enum KernelId {
+    K_HIST = 0, K_NODE_STARTS, K_NODE_TABLES, K_LEVEL_PASS, K_DD_COUNT, K_DD_SCAN, K_DD_WRITE,
+    K_Q_ACCESS, K_Q_RANK, K_Q_SELECT, K_Q_MULTI, K_COUNT
+};
+const char *kKernelNames[K_COUNT] = {"histogram", "node_starts", "node_tables", "level_pass", "dd_count",
+                                     "dd_scan",   "dd_write",    "query_access", "query_rank", "query_select",
+                                     "query_multi"};
+
+struct ProfRecord {
+    int kid;
+    double bytes;
+    cudaEvent_t e0, e1;
+};
+
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<ProfRecord> recs;
+    std::vector<cudaEvent_t> pool;
+
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+};
+Profiler g_prof;
+
+// Brackets one launch; a no-op when profiling is off.
+struct ProfScope {
+    int idx = -1;
+    cudaStream_t st;
+    ProfScope(int kid, double bytes, cudaStream_t s) : st(s) {
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (!g_prof.on) return;
+        ProfRecord r{kid, bytes, g_prof.take(), g_prof.take()};
+        if (!r.e0 || !r.e1) return;
+        cudaEventRecord(r.e0, st);
+        idx = (int)g_prof.recs.size();
+        g_prof.recs.push_back(r);
+    }
+    ~ProfScope() {
+        if (idx < 0) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        cudaEventRecord(g_prof.recs[idx].e1, st);
+    }
+};
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+wt_status check_args(const void *S, uint64_t n, uint64_t sigma, int width) {
+    if (width != 1 && width != 2 && width != 4) return WT_ERR_ARG;
+    if (sigma == 0 || sigma > WT_MAX_SIGMA) return WT_ERR_ARG;
+    if (width < 4 && sigma > (1ull << (8 * width))) return WT_ERR_ARG;
+    if (n > 0 && S == nullptr) return WT_ERR_ARG;
+    if (n >= (1ull << 56)) return WT_ERR_ARG;
+    return WT_OK;
+}
+
+// Per-level sizes of the serialised layout.
+struct Shape {
+    uint64_t n, nblocks, nspans, ncap;
+    size_t words, R, Hy, S;
+};
+
+Shape shape_of(uint64_t n) {
+    Shape s;
+    s.n = n;
+    s.nblocks = ceil_div(n, kBlockBits);
+    s.nspans = ceil_div(n, 1ull << kSpanShift);
+    s.ncap = n / kSample + 2;
+    s.words = align256(s.nblocks * 64);
+    s.R = align256((s.nblocks + 1) * 4);
+    s.Hy = align256((s.nspans + 1) * 8);
+    s.S = align256(s.ncap * 4);
+    return s;
+}
+
+}  // namespace
+
+struct wt_tree {
+    uint64_t n = 0, sigma = 0;
+    uint32_t L = 0;
+    int width = 0;
+    int variant = WT_VARIANT_LEVELWISE;
+    Allocator alloc{};
+    void *mem = nullptr;
+    size_t mem_bytes = 0;
+    TreeDesc *d_desc = nullptr;
+    uint32_t *d_err = nullptr;
+    TreeDesc h_desc{};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool finalized = false;
+    wt_status status = WT_OK;
+};
+
+namespace {
+
+// Allocates the resident part of a tree: descriptor, error word and every
+// level's bitmap and directories, and fills the host descriptor.
+wt_status tree_alloc(wt_tree *t, cudaStream_t st) {
+    const Shape s = shape_of(t->n);
+    const size_t per_level = s.words + s.R + s.Hy + 2 * s.S;
+    t->mem_bytes = align256(sizeof(TreeDesc)) + 256 + per_level * t->L;
+    t->mem = dev_alloc(t->alloc, t->mem_bytes, st);
+    if (!t->mem) return WT_ERR_OOM;
+    char *p = static_cast<char *>(t->mem);
+    t->d_desc = reinterpret_cast<TreeDesc *>(p);
+    p += align256(sizeof(TreeDesc));
+    t->d_err = reinterpret_cast<uint32_t *>(p);
+    p += 256;
+    memset(&t->h_desc, 0, sizeof(TreeDesc));
+    t->h_desc.n = t->n;
+    t->h_desc.sigma = t->sigma;
+    t->h_desc.nblocks = s.nblocks;
+    t->h_desc.L = t->L;
+    t->h_desc.width = (uint32_t)t->width;
+    for (uint32_t l = 0; l < t->L; l++) {
+        LevelDesc &d = t->h_desc.lv[l];
+        d.words = reinterpret_cast<uint32_t *>(p);
+        p += s.words;
+        d.R = reinterpret_cast<uint32_t *>(p);
+        p += s.R;
+        d.Hy = reinterpret_cast<uint64_t *>(p);
+        p += s.Hy;
+        d.S1 = reinterpret_cast<uint32_t *>(p);
+        p += s.S;
+        d.S0 = reinterpret_cast<uint32_t *>(p);
+        p += s.S;
+        d.ones = 0;
+    }
+    return WT_OK;
+}
+
+#define WT_CK(expr)                                  \
+    do {                                             \
+        if ((expr) != cudaSuccess) {                 \
+            cudaGetLastError();                      \
+            return WT_ERR_CUDA;                      \
+        }                                            \
+    } while (0)
+
+// Scratch of one level-wise build.
+struct Scratch {
+    void *mem = nullptr;
+    size_t bytes = 0;
+    BuildScratch b{};
+};
+
+wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t sigma, uint32_t L, int width,
+                        bool need_levels, cudaStream_t st) {
+    const uint64_t ntiles = ceil_div(n, lw_tile_elems());
+    const size_t hist = align256(sigma * 8);
+    const size_t hex = align256(((1ull << L) + 1) * 8);
+    const size_t tab = need_levels ? align256((1ull << L) * 8) : 0;
+    const size_t status = need_levels ? align256((size_t)L * ntiles * 8) : 0;
+    const size_t tickets = need_levels ? align256((size_t)L * 4) : 0;
+    const size_t zeroed = hist + status + tickets;
+    const size_t buf = align256(n * (uint64_t)width);
+    const int nbuf = need_levels ? (L >= 3 ? 2 : (L == 2 ? 1 : 0)) : 0;
+    sc.bytes = zeroed + hex + 2 * tab + nbuf * buf;
+    sc.mem = dev_alloc(A, sc.bytes, st);
+    if (!sc.mem) return WT_ERR_OOM;
+    char *p = static_cast<char *>(sc.mem);
+    sc.b.hist = reinterpret_cast<uint64_t *>(p);
+    p += hist;
+    sc.b.status = reinterpret_cast<uint64_t *>(p);
+    p += status;
+    sc.b.tickets = reinterpret_cast<uint32_t *>(p);
+    p += tickets;
+    sc.b.hex = reinterpret_cast<uint64_t *>(p);
+    p += hex;
+    sc.b.ob = reinterpret_cast<uint64_t *>(p);
+    p += tab;
+    sc.b.ze = reinterpret_cast<uint64_t *>(p);
+    p += tab;
+    sc.b.ping = nbuf >= 1 ? p : nullptr;
+    p += nbuf >= 1 ? buf : 0;
+    sc.b.pong = nbuf >= 2 ? p : nullptr;
+    WT_CK(cudaMemsetAsync(sc.mem, 0, zeroed, st));
+    return WT_OK;
+}
+
+// The level-wise build (kernels a, a', then b + c per level) of a tree whose
+// memory is allocated, from device symbols S.
+wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
+    Scratch sc;
+    wt_status r = scratch_alloc(t->alloc, sc, t->n, t->sigma, t->L, t->width, true, st);
+    if (r != WT_OK) return r;
+    const BuildScratch &b = sc.b;
+    const double nw = (double)t->n * t->width;
+    {
+        ProfScope p(K_HIST, nw, st);
+        WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st));
+    }
+    if (t->L > 0) {
+        const double leaves = (double)(1ull << t->L);
+        {
+            ProfScope p(K_NODE_STARTS, 8.0 * (t->sigma + leaves + 1), st);
+            WT_CK(launch_node_starts(b.hist, t->sigma, t->L, t->n, b.hex, st));
+        }
+        {
+            ProfScope p(K_NODE_TABLES, 8.0 * 5 * leaves, st);
+            WT_CK(launch_node_tables(b.hex, t->L, b.ob, b.ze, st));
+        }
+        const uint64_t ntiles = ceil_div(t->n, lw_tile_elems());
+        const void *cur = S;
+        void *bufs[2] = {b.ping, b.pong};
+        for (uint32_t l = 0; l < t->L; l++) {
+            void *nxt = (l + 1 < t->L) ? bufs[l & 1] : nullptr;
+            // read P_l, write the bitmap (n/8) and its directory (n/128), scatter P_{l+1}
+            const double bytes = nw + t->n / 8.0 + t->n / 128.0 + (nxt ? nw : 0.0);
+            ProfScope p(K_LEVEL_PASS, bytes, st);
+            WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
+                                    &t->d_desc->lv[l].ones, b.status + l * ntiles, b.tickets + l, t->d_err, st));
+            cur = nxt;
+        }
+    }
+    dev_free(t->alloc, sc.mem, sc.bytes, st);
+    return WT_OK;
+}
+
+wt_status enqueue_build(wt_tree *t, const void *S, int variant, cudaStream_t st) {
+    // Descriptor (with level pointers; "ones" is filled by the level passes)
+    // and a zero error word.
+    WT_CK(cudaMemcpyAsync(t->d_desc, &t->h_desc, sizeof(TreeDesc), cudaMemcpyHostToDevice, st));
+    WT_CK(cudaMemsetAsync(t->d_err, 0, sizeof(uint32_t), st));
+    if (t->n == 0) {
+        // Empty levels: R[0] = Hy[0] = 0, ones = 0.
+        for (uint32_t l = 0; l < t->L; l++) {
+            WT_CK(cudaMemsetAsync(t->h_desc.lv[l].R, 0, 4, st));
+            WT_CK(cudaMemsetAsync(t->h_desc.lv[l].Hy, 0, 8, st));
+        }
+        return WT_OK;
+    }
+    (void)variant;
+    t->variant = WT_VARIANT_LEVELWISE;
+    return enqueue_levelwise(t, S, st);
+}
+
+// Waits for the build, copies the per-level counts back and reads the error word.
+wt_status finalize(wt_tree *t) {
+    if (t->finalized) return t->status;
+    t->finalized = true;
+    if (cudaEventSynchronize(t->done) != cudaSuccess) {
+        cudaGetLastError();
+        return t->status = WT_ERR_CUDA;
+    }
+    uint32_t err = 0;
+    TreeDesc d;
+    if (cudaMemcpy(&d, t->d_desc, sizeof(TreeDesc), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&err, t->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return t->status = WT_ERR_CUDA;
+    }
+    for (uint32_t l = 0; l < t->L; l++) t->h_desc.lv[l].ones = d.lv[l].ones;
+    if (err & kErrSymbol)
+        t->status = WT_ERR_SYMBOL_RANGE;
+    else if (err & kErrTimeout)
+        t->status = WT_ERR_TIMEOUT;
+    return t->status;
+}
+
+// Stream-ordered release: the memory returns to the allocator after the work
+// already queued on the build stream; the host does not wait.
+void tree_destroy(wt_tree *t) {
+    if (!t) return;
+    if (t->done) cudaEventDestroy(t->done);
+    if (t->mem) dev_free(t->alloc, t->mem, t->mem_bytes, t->stream);
+    delete t;
+}
+
+wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int variant, cudaStream_t st) {
+    wt_status r = check_args(S, n, sigma, width);
+    if (r != WT_OK) {
+        set_last(r);
+        return nullptr;
+    }
+    if (variant < WT_VARIANT_AUTO || variant > WT_VARIANT_DD) {
+        set_last(WT_ERR_ARG);
+        return nullptr;
+    }
+    wt_tree *t = new (std::nothrow) wt_tree();
+    if (!t) {
+        set_last(WT_ERR_OOM);
+        return nullptr;
+    }
+    t->n = n;
+    t->sigma = sigma;
+    t->L = levels_of(sigma);
+    t->width = width;
+    t->stream = st;
+    t->alloc = current_allocator();
+    if (cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete t;
+        set_last(WT_ERR_CUDA);
+        return nullptr;
+    }
+    r = tree_alloc(t, st);
+    const void *Sd = S;
+    void *staged = nullptr;
+    const size_t sbytes = n * (uint64_t)width;
+    if (r == WT_OK && n > 0 && !is_device_pointer(S)) {
+        staged = dev_alloc(t->alloc, sbytes, st);
+        if (!staged)
+            r = WT_ERR_OOM;
+        else if (cudaMemcpyAsync(staged, S, sbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            r = WT_ERR_CUDA;
+        }
+        Sd = staged;
+    }
+    if (r == WT_OK) r = enqueue_build(t, Sd, variant, st);
+    if (staged) dev_free(t->alloc, staged, sbytes, st);
+    if (r == WT_OK && cudaEventRecord(t->done, st) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    if (r != WT_OK) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        t->finalized = true;
+        tree_destroy(t);
+        set_last(r);
+        return nullptr;
+    }
+    set_last(WT_OK);
+    return t;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+wt_handle wt_build(const void *S, uint64_t n, uint64_t sigma, int sym_width) {
+    wt_handle h = build_async(S, n, sigma, sym_width, WT_VARIANT_AUTO, nullptr);
+    if (!h) return nullptr;
+    wt_status r = finalize(h);
+    if (r != WT_OK) {
+        tree_destroy(h);
+        set_last(r);
+        return nullptr;
+    }
+    set_last(WT_OK);
+    return h;
+}
+
+wt_handle wt_build_async(const void *S, uint64_t n, uint64_t sigma, int sym_width, int variant, void *stream) {
+    return build_async(S, n, sigma, sym_width, variant, static_cast<cudaStream_t>(stream));
+}
+
+wt_status wt_wait(wt_handle h) {
+    if (!h) return set_last(WT_ERR_ARG);
+    return set_last(finalize(h));
+}
+
+wt_status wt_build_batch(const void *const *S, const uint64_t *n, const uint64_t *sigma, const int *sym_width,
+                         uint32_t count, wt_handle *out, void *stream) {
+    if (count > 0 && (!S || !n || !sigma || !sym_width || !out)) return set_last(WT_ERR_ARG);
+    wt_status first = WT_OK;
+    for (uint32_t k = 0; k < count; k++) {
+        out[k] = build_async(S[k], n[k], sigma[k], sym_width[k], WT_VARIANT_AUTO,
+                             static_cast<cudaStream_t>(stream));
+        if (!out[k] && first == WT_OK) first = g_last;
+    }
+    return set_last(first);
+}
+
+wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, void *stream) {
+    if (!h || (m && (!i || !out))) return set_last(WT_ERR_ARG);
+    ProfScope p(K_Q_ACCESS, 16.0 * m, static_cast<cudaStream_t>(stream));
+    if (launch_access(h->d_desc, i, m, out, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_last(WT_ERR_CUDA);
+    }
+    return set_last(WT_OK);
+}
+
+wt_status wt_rank(wt_handle h, const uint32_t *c, const uint64_t *i, uint64_t m, uint64_t *out, void *stream) {
+    if (!h || (m && (!c || !i || !out))) return set_last(WT_ERR_ARG);
+    ProfScope p(K_Q_RANK, 16.0 * m, static_cast<cudaStream_t>(stream));
+    if (launch_rank(h->d_desc, c, i, m, out, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_last(WT_ERR_CUDA);
+    }
+    return set_last(WT_OK);
+}
+
+wt_status wt_select(wt_handle h, const uint32_t *c, const uint64_t *j, uint64_t m, uint64_t *out, void *stream) {
+    if (!h || (m && (!c || !j || !out))) return set_last(WT_ERR_ARG);
+    ProfScope p(K_Q_SELECT, 16.0 * m, static_cast<cudaStream_t>(stream));
+    if (launch_select(h->d_desc, c, j, m, out, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_last(WT_ERR_CUDA);
+    }
+    return set_last(WT_OK);
+}
+
+wt_status wt_query_multi(const wt_handle *trees, uint32_t ntrees, const uint32_t *tree_idx, const uint8_t *op,
+                         const uint32_t *c, const uint64_t *arg, uint64_t m, uint64_t *out, void *stream) {
+    if (m == 0) return set_last(WT_OK);
+    if (!trees || ntrees == 0 || !tree_idx || !op || !c || !arg || !out) return set_last(WT_ERR_ARG);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<const TreeDesc *> ptrs(ntrees);
+    for (uint32_t k = 0; k < ntrees; k++) {
+        if (!trees[k]) return set_last(WT_ERR_ARG);
+        ptrs[k] = trees[k]->d_desc;
+    }
+    const Allocator A = current_allocator();
+    const size_t bytes = ntrees * sizeof(TreeDesc *);
+    void *d = dev_alloc(A, bytes, st);
+    if (!d) return set_last(WT_ERR_OOM);
+    wt_status r = WT_OK;
+    ProfScope p(K_Q_MULTI, 25.0 * m, st);
+    if (cudaMemcpyAsync(d, ptrs.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        launch_query_multi(static_cast<const TreeDesc *const *>(d), tree_idx, op, c, arg, m, out, st) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    dev_free(A, d, bytes, st);
+    return set_last(r);
+}
+
+wt_status wt_free(wt_handle h) {
+    if (!h) return set_last(WT_ERR_ARG);
+    tree_destroy(h);
+    return set_last(WT_OK);
+}
+
+wt_status wt_info(wt_handle h, wt_info_t *out) {
+    if (!h || !out) return set_last(WT_ERR_ARG);
+    finalize(h);
+    out->n = h->n;
+    out->sigma = h->sigma;
+    out->levels = h->L;
+    out->sym_width = h->width;
+    out->variant = h->variant;
+    out->reserved = 0;
+    out->device_bytes = h->mem_bytes;
+    return set_last(h->status);
+}
+
+wt_status wt_level_view(wt_handle h, uint32_t l, wt_level_view_t *out) {
+    if (!h || !out || l >= h->L) return set_last(WT_ERR_ARG);
+    finalize(h);
+    const Shape s = shape_of(h->n);
+    const LevelDesc &d = h->h_desc.lv[l];
+    out->words = d.words;
+    out->R = d.R;
+    out->Hy = d.Hy;
+    out->S1 = d.S1;
+    out->S0 = d.S0;
+    out->ones = d.ones;
+    out->n_words = s.nblocks * 16;
+    out->n_R = s.nblocks + 1;
+    out->n_Hy = s.nspans + 1;
+    out->n_S1 = ceil_div(d.ones, kSample);
+    out->n_S0 = ceil_div(h->n - d.ones, kSample);
+    return set_last(h->status);
+}
+
+wt_status wt_set_allocator(void *(*alloc)(size_t, void *, void *), void (*free_)(void *, size_t, void *, void *),
+                           void *ctx) {
+    if ((alloc == nullptr) != (free_ == nullptr)) return set_last(WT_ERR_ARG);
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = {alloc, free_, ctx};
+    return set_last(WT_OK);
+}
+
+wt_status wt_profile_begin(void) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (auto &r : g_prof.recs) {
+        g_prof.pool.push_back(r.e0);
+        g_prof.pool.push_back(r.e1);
+    }
+    g_prof.recs.clear();
+    g_prof.on = true;
+    return set_last(WT_OK);
+}
+
+wt_status wt_profile_end(wt_kernel_stat_t *out, uint32_t cap, uint32_t *count) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = false;
+    wt_kernel_stat_t acc[K_COUNT];
+    memset(acc, 0, sizeof(acc));
+    wt_status r = WT_OK;
+    for (auto &rec : g_prof.recs) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(rec.e1) != cudaSuccess || cudaEventElapsedTime(&ms, rec.e0, rec.e1) != cudaSuccess) {
+            cudaGetLastError();
+            r = WT_ERR_CUDA;
+            continue;
+        }
+        acc[rec.kid].launches++;
+        acc[rec.kid].total_ms += ms;
+        acc[rec.kid].alg_bytes += rec.bytes;
+        g_prof.pool.push_back(rec.e0);
+        g_prof.pool.push_back(rec.e1);
+    }
+    g_prof.recs.clear();
+    uint32_t k = 0;
+    for (int id = 0; id < K_COUNT; id++) {
+        if (!acc[id].launches) continue;
+        if (out && k < cap) {
+            out[k] = acc[id];
+            strncpy(out[k].name, kKernelNames[id], sizeof(out[k].name) - 1);
+        }
+        k++;
+    }
+    if (count) *count = k;
+    return set_last(r);
+}
+
+wt_status wt_last_status(void) { return g_last; }
+
+const char *wt_status_string(wt_status s) {
+    switch (s) {
+        case WT_OK: return "ok";
+        case WT_ERR_ARG: return "invalid argument";
+        case WT_ERR_SYMBOL_RANGE: return "symbol out of range";
+        case WT_ERR_OOM: return "out of device memory";
+        case WT_ERR_CUDA: return "CUDA error";
+        case WT_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+wt_status wt_node_starts(const void *S, uint64_t n, uint64_t sigma, int sym_width, uint64_t *Hex, void *stream) {
+    wt_status r = check_args(S, n, sigma, sym_width);
+    if (r != WT_OK || !Hex) return set_last(r != WT_OK ? r : WT_ERR_ARG);
+    if (n > 0 && !is_device_pointer(S)) return set_last(WT_ERR_ARG);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Allocator A = current_allocator();
+    const uint32_t L = levels_of(sigma);
+    const size_t bytes = align256(sigma * 8) + 256;
+    void *mem = dev_alloc(A, bytes, st);
+    if (!mem) return set_last(WT_ERR_OOM);
+    uint64_t *hist = static_cast<uint64_t *>(mem);
+    uint32_t *err = reinterpret_cast<uint32_t *>(static_cast<char *>(mem) + align256(sigma * 8));
+    uint32_t herr = 0;
+    if (cudaMemsetAsync(mem, 0, bytes, st) != cudaSuccess ||
+        launch_histogram(S, n, sym_width, sigma, hist, err, st) != cudaSuccess ||
+        launch_node_starts(hist, sigma, L, n, Hex, st) != cudaSuccess ||
+        cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    dev_free(A, mem, bytes, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    if (r == WT_OK && (herr & kErrSymbol)) r = WT_ERR_SYMBOL_RANGE;
+    return set_last(r);
+}
+
+wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_width, uint32_t l, const uint64_t *Hex,
+                        uint32_t *words, uint32_t *R, void *nxt, void *stream) {
+    wt_status r = check_args(cur, n, sigma, sym_width);
+    if (r != WT_OK) return set_last(r);
+    const uint32_t L = levels_of(sigma);
+    if (l >= L || !Hex || (n > 0 && (!words || !R))) return set_last(WT_ERR_ARG);
+    if (n == 0) return set_last(WT_OK);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Allocator A = current_allocator();
+    const Shape s = shape_of(n);
+    const uint64_t ntiles = ceil_div(n, lw_tile_elems());
+    // Scratch: node tables, look-back words, ticket, error word, and the
+    // directory parts this entry point does not return (Hy, S1, S0, ones).
+    const size_t tab = align256((1ull << L) * 8);
+    const size_t status = align256(ntiles * 8);
+    const size_t zeroed = status + 256;
+    const size_t bytes = zeroed + 2 * tab + s.Hy + 2 * s.S + 256;
+    void *mem = dev_alloc(A, bytes, st);
+    if (!mem) return set_last(WT_ERR_OOM);
+    char *p = static_cast<char *>(mem);
+    uint64_t *stw = reinterpret_cast<uint64_t *>(p);
+    p += status;
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(p);
+    uint32_t *err = ticket + 1;
+    p += 256;
+    uint64_t *ob = reinterpret_cast<uint64_t *>(p);
+    p += tab;
+    uint64_t *ze = reinterpret_cast<uint64_t *>(p);
+    p += tab;
+    LevelDesc lv;
+    lv.words = words;
+    lv.R = R;
+    lv.Hy = reinterpret_cast<uint64_t *>(p);
+    p += s.Hy;
+    lv.S1 = reinterpret_cast<uint32_t *>(p);
+    p += s.S;
+    lv.S0 = reinterpret_cast<uint32_t *>(p);
+    p += s.S;
+    uint64_t *ones = reinterpret_cast<uint64_t *>(p);
+    lv.ones = 0;
+    uint32_t herr = 0;
+    if (cudaMemsetAsync(mem, 0, zeroed, st) != cudaSuccess ||
+        launch_node_tables(Hex, L, ob, ze, st) != cudaSuccess ||
+        launch_level_pass(cur, (l + 1 < L) ? nxt : nullptr, n, sym_width, L, l, ob, ze, lv, ones, stw, ticket, err,
+                          st) != cudaSuccess ||
+        cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    dev_free(A, mem, bytes, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    if (r == WT_OK && (herr & kErrTimeout)) r = WT_ERR_TIMEOUT;
+    return set_last(r);
+}
+
+}  // extern "C"

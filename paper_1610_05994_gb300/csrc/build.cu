@@ -1,0 +1,434 @@
+// build.cu -- construction kernels of the level-wise path.
+//
+// (a)  histogram of the leaf codes + exclusive scan  -> Hex (node starts of
+//      every level at once: node v of level l starts at Hex[v << (L - l)]),
+//      replacing the per-level "count" and parPrefixSum steps of Algorithm 1.
+// (a') per-level node tables OB / ZE from Hex.
+// (b+c) one fused pass per level over P_l: the level-l bit of every symbol is
+//      packed into the bitmap, a decoupled look-back scan gives the ones
+//      before every position, the rank/select directory entries are written
+//      from it, and every symbol is placed at its position in P_{l+1}:
+//         bit 0:  dst = zeros_before(p) + OB_l[v]
+//         bit 1:  dst = ones_before(p)  + ZE_l[v]
+//      where v = key_l(s), OB_l[v] = ones on level l before node v's start,
+//      ZE_l[v] = zeros on level l up to node v's end.  This is the stable
+//      counting-sort placement of Algorithm 1 ("bitmapSetBit at C[node]++")
+//      written as a closed form of two prefix counts.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wt_internal.cuh"
+
+namespace wt {
+
+// ------------------------------------------------------------------ (a)
+
+constexpr int kHistThreads = 512;
+constexpr uint32_t kHistSmemBins = 48 * 1024;  // u32 bins per CTA for the shared-memory path
+
+template <typename Sym>
+__device__ __forceinline__ void hist_add_shared(uint32_t *bins, uint32_t sigma, uint32_t s, bool &bad) {
+    if (s < sigma)
+        atomicAdd(&bins[s], 1u);
+    else
+        bad = true;
+}
+
+// Shared-memory histogram: `copies` private copies of the sigma bins (warp w
+// uses copy w % copies) spread same-bin contention for small alphabets.
+template <typename Sym>
+__global__ void __launch_bounds__(kHistThreads) hist_shared_kernel(const Sym *__restrict__ S, uint64_t n,
+                                                                   uint32_t sigma, uint32_t copies,
+                                                                   uint64_t *__restrict__ hist,
+                                                                   uint32_t *__restrict__ err) {
+    extern __shared__ uint32_t bins[];
+    const uint32_t total = sigma * copies;
+    for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) bins[k] = 0;
+    __syncthreads();
+    uint32_t *mine = bins + ((threadIdx.x >> 5) % copies) * sigma;
+    bool bad = false;
+    constexpr int kPer = 16 / sizeof(Sym);
+    const bool vec = (reinterpret_cast<uintptr_t>(S) & 15) == 0;
+    const uint64_t nvec = vec ? n / kPer : 0;
+    const uint4 *V = reinterpret_cast<const uint4 *>(S);
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < nvec;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        uint4 q = __ldcs(V + k);
+        const Sym *e = reinterpret_cast<const Sym *>(&q);
+#pragma unroll
+        for (int t = 0; t < kPer; t++) hist_add_shared<Sym>(mine, sigma, (uint32_t)e[t], bad);
+    }
+    for (uint64_t k = nvec * kPer + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+         k += (uint64_t)gridDim.x * blockDim.x)
+        hist_add_shared<Sym>(mine, sigma, (uint32_t)S[k], bad);
+    if (bad) atomicOr(err, kErrSymbol);
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < sigma; c += blockDim.x) {
+        uint32_t sum = 0;
+        for (uint32_t k = 0; k < copies; k++) sum += bins[k * sigma + c];
+        if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&hist[c]), (unsigned long long)sum);
+    }
+}
+
+// Large alphabets: global 64-bit atomics, one per group of equal codes in a warp.
+template <typename Sym>
+__global__ void __launch_bounds__(kHistThreads) hist_global_kernel(const Sym *__restrict__ S, uint64_t n,
+                                                                   uint64_t sigma, uint64_t *__restrict__ hist,
+                                                                   uint32_t *__restrict__ err) {
+    bool bad = false;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t start = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t rounds = ceil_div(n, stride);
+    for (uint64_t r = 0; r < rounds; r++) {
+        const uint64_t k = start + r * stride;
+        const bool valid = k < n;
+        uint32_t s = valid ? (uint32_t)S[k] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, s);
+        const int leader = __ffs(peers) - 1;
+        if (valid) {
+            if ((uint64_t)s >= sigma)
+                bad = true;
+            else if ((threadIdx.x & 31) == leader)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&hist[s]), (unsigned long long)__popc(peers));
+        }
+    }
+    if (bad) atomicOr(err, kErrSymbol);
+}
+
+static int sm_count() {
+    static int count = 0;
+    if (!count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+        if (count <= 0) count = 1;
+    }
+    return count;
+}
+
+template <typename Sym>
+static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64_t *hist, uint32_t *err,
+                               cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const Sym *s = static_cast<const Sym *>(S);
+    const uint64_t per_cta_cap = 1ull << 30;  // keeps every u32 shared bin below 2^32
+    uint64_t grid = (uint64_t)sm_count() * 4;
+    grid = grid > ceil_div(n, per_cta_cap) ? grid : ceil_div(n, per_cta_cap);
+    uint64_t want = ceil_div(n, (uint64_t)kHistThreads * 16);
+    if (grid > want) grid = want ? want : 1;
+    if (sigma <= kHistSmemBins) {
+        uint32_t sig = (uint32_t)sigma;
+        uint32_t copies = (uint32_t)(kHistSmemBins / sigma);
+        const uint32_t warps = kHistThreads / 32;
+        if (copies > warps) copies = warps;
+        if (copies < 1) copies = 1;
+        size_t smem = (size_t)sig * copies * sizeof(uint32_t);
+        cudaError_t e = cudaFuncSetAttribute(hist_shared_kernel<Sym>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        hist_shared_kernel<Sym><<<(unsigned)grid, kHistThreads, smem, st>>>(s, n, sig, copies, hist, err);
+    } else {
+        hist_global_kernel<Sym><<<(unsigned)grid, kHistThreads, 0, st>>>(s, n, sigma, hist, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_histogram(const void *S, uint64_t n, int width, uint64_t sigma, uint64_t *hist, uint32_t *err,
+                             cudaStream_t st) {
+    switch (width) {
+        case 1: return histogram_t<uint8_t>(S, n, sigma, hist, err, st);
+        case 2: return histogram_t<uint16_t>(S, n, sigma, hist, err, st);
+        case 4: return histogram_t<uint32_t>(S, n, sigma, hist, err, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+constexpr int kScanThreads = 1024;
+
+// Exclusive scan of the values of one CTA's threads (one value per thread).
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint64_t w = lane < nw ? s_warp[lane] : 0;
+        uint64_t winc = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, winc, d);
+            if (lane >= d) winc += y;
+        }
+        if (lane < nw) s_warp[lane] = winc - w;
+    }
+    __syncthreads();
+    const uint64_t r = s_warp[warp] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+// Hex[c] = sum of hist[c'] over c' < c, c = 0 .. 2^L (bins at c >= sigma count 0).
+__global__ void __launch_bounds__(kScanThreads) node_starts_kernel(const uint64_t *__restrict__ hist,
+                                                                   uint64_t sigma, uint64_t entries,
+                                                                   uint64_t *__restrict__ hex) {
+    __shared__ uint64_t s_warp[32];
+    const uint64_t chunk = ceil_div(entries, blockDim.x);
+    const uint64_t lo = threadIdx.x * chunk;
+    const uint64_t hi = lo + chunk < entries ? lo + chunk : entries;
+    uint64_t sum = 0;
+    for (uint64_t c = lo; c < hi; c++) sum += c < sigma ? hist[c] : 0;
+    uint64_t run = block_exclusive_scan(sum, s_warp);
+    for (uint64_t c = lo; c < hi; c++) {
+        hex[c] = run;
+        run += c < sigma ? hist[c] : 0;
+    }
+}
+
+cudaError_t launch_node_starts(const uint64_t *hist, uint64_t sigma, uint32_t L, uint64_t n, uint64_t *hex,
+                               cudaStream_t st) {
+    (void)n;
+    node_starts_kernel<<<1, kScanThreads, 0, st>>>(hist, sigma, (1ull << L) + 1, hex);
+    return cudaGetLastError();
+}
+
+// One CTA per level l: Z_l[v] = size of the left child of node v =
+// Hex[(2v+1) << (L-l-1)] - Hex[2v << (L-l-1)]; ZB_l = exclusive scan of Z_l;
+// OB_l[v] = Hex[v << (L-l)] - ZB_l[v]; ZE_l[v] = ZB_l[v] + Z_l[v].
+// Level l's tables start at offset 2^l - 1.
+__global__ void __launch_bounds__(kScanThreads) node_tables_kernel(const uint64_t *__restrict__ hex, uint32_t L,
+                                                                   uint64_t *__restrict__ ob,
+                                                                   uint64_t *__restrict__ ze) {
+    __shared__ uint64_t s_warp[32];
+    const uint32_t l = blockIdx.x;
+    const uint64_t nodes = 1ull << l;
+    const uint32_t sh = L - l;  // >= 1
+    const uint64_t chunk = ceil_div(nodes, blockDim.x);
+    const uint64_t lo = threadIdx.x * chunk < nodes ? threadIdx.x * chunk : nodes;
+    const uint64_t hi = lo + chunk < nodes ? lo + chunk : nodes;
+    uint64_t sum = 0;
+    for (uint64_t v = lo; v < hi; v++) sum += hex[(2 * v + 1) << (sh - 1)] - hex[(2 * v) << (sh - 1)];
+    uint64_t zb = block_exclusive_scan(sum, s_warp);
+    uint64_t *obl = ob + (nodes - 1), *zel = ze + (nodes - 1);
+    for (uint64_t v = lo; v < hi; v++) {
+        const uint64_t z = hex[(2 * v + 1) << (sh - 1)] - hex[(2 * v) << (sh - 1)];
+        obl[v] = hex[v << sh] - zb;
+        zel[v] = zb + z;
+        zb += z;
+    }
+}
+
+cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, uint64_t *ze, cudaStream_t st) {
+    if (L == 0) return cudaSuccess;
+    node_tables_kernel<<<L, kScanThreads, 0, st>>>(hex, L, ob, ze);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ (b + c)
+
+constexpr int kLwThreads = 256;
+constexpr int kLwItems = 16;                      // consecutive symbols per thread
+constexpr int kLwTile = kLwThreads * kLwItems;    // 4096 symbols = 8 rank blocks
+constexpr int kLwWarps = kLwThreads / 32;         // one warp = one 512-bit block
+static_assert(kLwItems * 32 == (int)kBlockBits, "a warp covers exactly one rank block");
+
+uint32_t lw_tile_elems() { return kLwTile; }
+
+struct LevelArgs {
+    const void *cur;
+    void *nxt;            // nullptr on the last level
+    uint64_t n;
+    uint64_t nblocks;
+    uint64_t nspans;
+    uint32_t L, l;
+    uint32_t ntiles;
+    LevelDesc lv;
+    uint64_t *ones_out;
+    const uint64_t *ob;   // level l's table (already offset)
+    const uint64_t *ze;
+    uint64_t *status;     // ntiles look-back words of this level
+    uint32_t *ticket;
+    uint32_t *err;
+};
+
+template <typename Sym>
+__device__ __forceinline__ void load_items(const Sym *__restrict__ src, uint64_t base, uint32_t p0, uint32_t cnt,
+                                           bool vec_ok, Sym (&v)[kLwItems]) {
+    if (vec_ok && p0 + kLwItems <= cnt) {
+        constexpr int kVec = kLwItems * sizeof(Sym) / 16;
+        const uint4 *q = reinterpret_cast<const uint4 *>(src + base + p0);
+        uint4 r[kVec];
+#pragma unroll
+        for (int k = 0; k < kVec; k++) r[k] = __ldcs(q + k);
+        const Sym *e = reinterpret_cast<const Sym *>(r);
+#pragma unroll
+        for (int k = 0; k < kLwItems; k++) v[k] = e[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < kLwItems; k++) v[k] = (p0 + k < cnt) ? src[base + p0 + k] : Sym(0);
+    }
+}
+
+template <typename Sym>
+__global__ void __launch_bounds__(kLwThreads) level_pass_kernel(LevelArgs a) {
+    __shared__ __align__(16) Sym s_split[kLwTile];
+    __shared__ uint32_t s_warp_excl[kLwWarps];
+    __shared__ uint64_t s_prefix;
+    __shared__ uint32_t s_tile, s_tile_ones;
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // A symbol-range fault found by the histogram (earlier on the stream)
+    // makes the node tables inconsistent with the data: skip the pass.
+    if (*(volatile uint32_t *)a.err & kErrSymbol) return;
+    if (t == 0) s_tile = atomicAdd(a.ticket, 1u);  // tiles in issue order: look-back waits only on earlier ones
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t base = (uint64_t)tile * kLwTile;
+    const uint32_t cnt = (uint32_t)((a.n - base) < (uint64_t)kLwTile ? (a.n - base) : (uint64_t)kLwTile);
+    const uint32_t p0 = t * kLwItems;
+    const Sym *cur = static_cast<const Sym *>(a.cur);
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(cur) & 15) == 0;
+
+    Sym v[kLwItems];
+    load_items<Sym>(cur, base, p0, cnt, vec_ok, v);
+
+    // Level-l bits of this thread's 16 symbols (bit k = symbol p0 + k).
+    const uint32_t sh = a.L - 1 - a.l;
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < kLwItems; k++) m |= (p0 + k < cnt ? ((uint32_t)v[k] >> sh) & 1u : 0u) << k;
+    const uint32_t c = __popc(m);
+
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    const uint32_t lane_excl = inc - c;
+    if (lane == 31) s_warp_excl[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < kLwWarps ? s_warp_excl[lane] : 0;
+        uint32_t winc = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, winc, d);
+            if (lane >= d) winc += y;
+        }
+        const uint32_t tile_ones = __shfl_sync(0xffffffffu, winc, kLwWarps - 1);
+        const uint64_t prefix = lookback_prefix(a.status, tile, tile_ones, a.err);
+        if (lane < kLwWarps) s_warp_excl[lane] = winc - w;
+        if (lane == 0) {
+            s_prefix = prefix;
+            s_tile_ones = tile_ones;
+        }
+    }
+    __syncthreads();
+    const uint64_t prefix = s_prefix;               // ones before this tile
+    const uint32_t tile_ones = s_tile_ones;
+    const uint32_t ones_before = s_warp_excl[warp] + lane_excl;  // inside the tile, before p0
+    const uint64_t gpos = base + p0;
+    const uint64_t block = gpos >> 9;
+
+    // Bitmap: 16 bits per thread, one coalesced 16-bit store (padding bits are 0).
+    if (block < a.nblocks) reinterpret_cast<uint16_t *>(a.lv.words)[gpos >> 4] = (uint16_t)m;
+
+    // Rank directory: lane 0 of each warp owns one 512-bit block.
+    if (lane == 0 && block < a.nblocks) {
+        const uint64_t before = prefix + s_warp_excl[warp];
+        a.lv.R[block] = (uint32_t)before;
+        if ((block & kBlocksPerSpanMask) == 0) a.lv.Hy[block >> (kSpanShift - 9)] = before;
+    }
+
+    // Select samples: a thread's 16 positions share one block, so a sample
+    // that falls among them is just that block.
+    const uint32_t valid = cnt > p0 ? (cnt - p0 < (uint32_t)kLwItems ? cnt - p0 : (uint32_t)kLwItems) : 0;
+    if (valid) {
+        const uint64_t g1 = prefix + ones_before;
+        const uint64_t k1 = ceil_div(g1, kSample);
+        if (k1 * kSample < g1 + c) a.lv.S1[k1] = (uint32_t)block;
+        const uint64_t g0 = gpos - g1;
+        const uint64_t k0 = ceil_div(g0, kSample);
+        if (k0 * kSample < g0 + (valid - c)) a.lv.S0[k0] = (uint32_t)block;
+    }
+
+    if (tile == a.ntiles - 1 && t == 0) {
+        const uint64_t total = prefix + tile_ones;
+        a.lv.R[a.nblocks] = (uint32_t)total;
+        a.lv.Hy[a.nspans] = total;
+        *a.ones_out = total;
+    }
+
+    if (a.nxt == nullptr) return;
+
+    // (c) Stable split of the tile by the level bit into shared memory
+    // (zeros first, then ones, order kept), then coalesced placement.
+    const uint32_t Zt = cnt - tile_ones;
+    uint32_t o = ones_before;
+#pragma unroll
+    for (int k = 0; k < kLwItems; k++) {
+        if (p0 + k < cnt) {
+            const uint32_t b = (m >> k) & 1u;
+            s_split[b ? Zt + o : p0 + k - o] = v[k];
+            o += b;
+        }
+    }
+    __syncthreads();
+    Sym *nxt = static_cast<Sym *>(a.nxt);
+    const uint64_t zeros_prefix = base - prefix;  // zeros before this tile
+    const uint32_t shv = a.L - a.l;               // key_l = s >> (L - l)
+    const uint32_t nodes = 1u << a.l;
+    bool bad = false;
+    for (uint32_t q = t; q < cnt; q += kLwThreads) {
+        const Sym s = s_split[q];
+        const uint32_t node = (uint32_t)s >> shv;
+        if (node >= nodes) {  // only after an earlier fault: never index past the tables
+            bad = true;
+            continue;
+        }
+        const uint64_t dst = q < Zt ? zeros_prefix + q + __ldg(a.ob + node)
+                                    : prefix + (q - Zt) + __ldg(a.ze + node);
+        if (dst < a.n)
+            nxt[dst] = s;
+        else
+            bad = true;
+    }
+    if (bad) atomicOr(a.err, kErrTimeout);
+}
+
+cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
+                              const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out,
+                              uint64_t *status, uint32_t *ticket, uint32_t *err, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    LevelArgs a;
+    a.cur = cur;
+    a.nxt = (l + 1 < L) ? nxt : nullptr;
+    a.n = n;
+    a.nblocks = ceil_div(n, kBlockBits);
+    a.nspans = ceil_div(n, 1ull << kSpanShift);
+    a.L = L;
+    a.l = l;
+    a.ntiles = (uint32_t)ceil_div(n, kLwTile);
+    a.lv = lv;
+    a.ones_out = ones_out;
+    a.ob = ob + ((1ull << l) - 1);
+    a.ze = ze + ((1ull << l) - 1);
+    a.status = status;
+    a.ticket = ticket;
+    a.err = err;
+    switch (width) {
+        case 1: level_pass_kernel<uint8_t><<<a.ntiles, kLwThreads, 0, st>>>(a); break;
+        case 2: level_pass_kernel<uint16_t><<<a.ntiles, kLwThreads, 0, st>>>(a); break;
+        case 4: level_pass_kernel<uint32_t><<<a.ntiles, kLwThreads, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace wt

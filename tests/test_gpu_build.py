@@ -1,0 +1,123 @@
+"""GPU parity of construction: every bitmap word, directory entry and count of
+trees built by the CUDA path through the C ABI equals the CPU oracle's."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import compare_tree, needs_gpu, to_dev, wt
+from oracle import oracle as O
+from paper_1610_05994_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+WORKLOAD_SMALL = inputs.WORKLOADS["u8-uniform-2^20-s256"]
+
+
+def test_small_workload_bit_exact():
+    """2^20 uniform bytes over 256 codes (8 levels): the full tree equals the oracle's."""
+    W = wt()
+    S = WORKLOAD_SMALL.generate()
+    t = W.Tree.build(to_dev(S), WORKLOAD_SMALL.sigma)
+    compare_tree(t, S, WORKLOAD_SMALL.sigma)
+
+
+SIZES = [0, 1, 31, 32, 33, 511, 512, 513, 4095, 4096, 4097, 8193, 65535, 65537, 100003]
+
+
+@pytest.mark.parametrize("sigma", [1, 2, 3, 4, 5, 16, 17, 96, 256])
+@pytest.mark.parametrize("n", SIZES)
+def test_edge_shapes_u8(sigma, n):
+    W = wt()
+    S = inputs.zipf(n, sigma, 1.0, 1000 + n, np.uint8) if n else np.zeros(0, np.uint8)
+    t = W.Tree.build(to_dev(S), sigma)
+    compare_tree(t, S, sigma)
+
+
+@pytest.mark.parametrize("sigma,dtype", [(257, np.uint16), (1000, np.uint16), (65536, np.uint16),
+                                         (4, np.uint32), (1 << 20, np.uint32), ((1 << 20) + 3, np.uint32)])
+@pytest.mark.parametrize("n", [1, 513, 4097, 70001])
+def test_wide_symbols(sigma, dtype, n):
+    W = wt()
+    S = inputs.zipf(n, sigma, 1.2, 77 + n, dtype)
+    t = W.Tree.build(to_dev(S), sigma)
+    compare_tree(t, S, sigma)
+
+
+def test_host_input_and_unaligned_device_input():
+    """S may be host memory; a device S that is not 16-byte aligned takes the scalar path."""
+    W = wt()
+    sigma = 96
+    S = inputs.zipf(50001, sigma, 1.0, 5, np.uint8)
+    compare_tree(W.Tree.build(S, sigma), S, sigma)
+    D = to_dev(np.concatenate([np.zeros(3, np.uint8), S]))
+    compare_tree(W.Tree.build(D[3:], sigma), S, sigma)
+
+
+def test_many_tiles_zipf_multi_level_scatter():
+    """Several thousand tiles, skewed codes: the look-back and the scatter stay exact."""
+    W = wt()
+    sigma = 1 << 12
+    S = inputs.zipf(3_000_017, sigma, 1.2, 3, np.uint16)
+    t = W.Tree.build(to_dev(S), sigma)
+    compare_tree(t, S, sigma)
+
+
+def test_symbol_out_of_range_is_reported():
+    W = wt()
+    S = np.array([0, 1, 2, 3, 4, 1], dtype=np.uint8)
+    with pytest.raises(W.WTError) as e:
+        W.Tree.build(to_dev(S), 4)
+    assert e.value.status == W.ERR_SYMBOL_RANGE
+
+
+def test_invalid_arguments():
+    W = wt()
+    S = to_dev(np.zeros(10, np.uint8))
+    for sigma in (0, 257):
+        with pytest.raises(W.WTError) as e:
+            W.Tree.build(S, sigma)
+        assert e.value.status == W.ERR_ARG
+
+
+def test_node_starts_stage():
+    """Kernel (a): Hex equals the oracle's node starts."""
+    W = wt()
+    for sigma, dtype, n in ((256, np.uint8, 1 << 20), (96, np.uint8, 999_999), (4, np.uint8, 12345),
+                            (65536, np.uint16, 300_001), (1 << 20, np.uint32, 200_003)):
+        S = inputs.zipf(n, sigma, 1.0, 21, dtype)
+        got = W.node_starts(to_dev(S), sigma).cpu().numpy()
+        assert np.array_equal(got, O.node_starts(S, sigma)), sigma
+
+
+def test_level_step_stage():
+    """Kernels (b) + (c) one level at a time: bitmap and R of level l and the order P_{l+1}."""
+    W = wt()
+    for sigma, dtype, n in ((96, np.uint8, 100_003), (1 << 16, np.uint16, 70_001), (1 << 20, np.uint32, 50_000)):
+        S = inputs.zipf(n, sigma, 1.1, 8, dtype)
+        L = O.levels(sigma)
+        hx = W.node_starts(to_dev(S), sigma)
+        bits = O.build_bits(S, sigma)
+        for l in range(L):
+            P = O.level_order(S, sigma, l).astype(dtype)
+            words, R, nxt = W.level_step(to_dev(P), sigma, l, hx, want_next=l + 1 < L)
+            assert np.array_equal(words.cpu().numpy().view(np.uint8), bits[l]), (sigma, l)
+            assert np.array_equal(R.cpu().numpy(), O.directory(bits[l], n)["R"]), (sigma, l)
+            if l + 1 < L:
+                assert np.array_equal(nxt.cpu().numpy(), O.level_order(S, sigma, l + 1).astype(dtype)), (sigma, l)
+
+
+def test_async_build_on_stream_and_torch_allocator():
+    W = wt()
+    W.use_torch_allocator(True)
+    try:
+        sigma = 20
+        S = inputs.uniform(200_001, sigma, 9, np.uint8)
+        s = torch.cuda.Stream()
+        D = to_dev(S)
+        torch.cuda.synchronize()
+        t = W.Tree.build(D, sigma, stream=s, wait=False)
+        t.wait()
+        compare_tree(t, S, sigma)
+        t.free()
+    finally:
+        W.use_torch_allocator(False)

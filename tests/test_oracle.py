@@ -278,3 +278,20 @@ def test_directory_beyond_2_32_bits():
     assert np.array_equal(d["R"], want.astype(np.uint32))
     assert list(d["Hy"]) == [0, 1 << 32, n]
     assert d["ones"] == n and len(d["S1"]) == (n + 8191) // 8192
+
+
+@pytest.mark.parametrize("sigma", [1, 2, 3, 20, 96, 256, 1000])
+def test_node_starts_are_histogram_prefix(sigma):
+    """Hex from numpy's bincount and cumsum; node v of level l starts at Hex[v << (L-l)]."""
+    S = inputs.zipf(5000, sigma, 1.0, 13, inputs.sym_dtype(sigma))
+    L = O.levels(sigma)
+    H = np.bincount(S, minlength=1 << L)
+    want = np.concatenate([[0], np.cumsum(H)]).astype(np.uint64)
+    hx = O.node_starts(S, sigma)
+    assert np.array_equal(hx, want)
+    for l in range(L):
+        keys = O.level_order(S, sigma, l) >> (L - l)
+        for v in range(1 << l):
+            hits = np.flatnonzero(keys == v)
+            if len(hits):
+                assert hits[0] == hx[v << (L - l)]
