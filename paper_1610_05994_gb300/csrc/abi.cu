@@ -229,7 +229,7 @@ struct Scratch {
 
 wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t sigma, uint32_t L, int width,
                         bool need_levels, cudaStream_t st) {
-    const uint64_t ntiles = ceil_div(n, lw_tile_elems());
+    const uint64_t ntiles = ceil_div(n, lw_tile_elems(width));
     const size_t hist = align256(sigma * 8);
     const size_t hex = align256(((1ull << L) + 1) * 8);
     const size_t tab = need_levels ? align256((1ull << L) * 8) : 0;
@@ -283,7 +283,7 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
             ProfScope p(K_NODE_TABLES, 8.0 * 5 * leaves, st);
             WT_CK(launch_node_tables(b.hex, t->L, b.ob, b.ze, st));
         }
-        const uint64_t ntiles = ceil_div(t->n, lw_tile_elems());
+        const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
         const void *cur = S;
         void *bufs[2] = {b.ping, b.pong};
         for (uint32_t l = 0; l < t->L; l++) {
@@ -648,7 +648,7 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Allocator A = current_allocator();
     const Shape s = shape_of(n);
-    const uint64_t ntiles = ceil_div(n, lw_tile_elems());
+    const uint64_t ntiles = ceil_div(n, lw_tile_elems(sym_width));
     // Scratch: node tables, look-back words, ticket, error word, and the
     // directory parts this entry point does not return (Hy, S1, S0, ones).
     const size_t tab = align256((1ull << L) * 8);

@@ -4,16 +4,7 @@
 //      every level at once: node v of level l starts at Hex[v << (L - l)]),
 //      replacing the per-level "count" and parPrefixSum steps of Algorithm 1.
 // (a') per-level node tables OB / ZE from Hex.
-// (b+c) one fused pass per level over P_l: the level-l bit of every symbol is
-//      packed into the bitmap, a decoupled look-back scan gives the ones
-//      before every position, the rank/select directory entries are written
-//      from it, and every symbol is placed at its position in P_{l+1}:
-//         bit 0:  dst = zeros_before(p) + OB_l[v]
-//         bit 1:  dst = ones_before(p)  + ZE_l[v]
-//      where v = key_l(s), OB_l[v] = ones on level l before node v's start,
-//      ZE_l[v] = zeros on level l up to node v's end.  This is the stable
-//      counting-sort placement of Algorithm 1 ("bitmapSetBit at C[node]++")
-//      written as a closed form of two prefix counts.
+// The fused level pass (b + c) is in level.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -226,208 +217,6 @@ __global__ void __launch_bounds__(kScanThreads) node_tables_kernel(const uint64_
 cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, uint64_t *ze, cudaStream_t st) {
     if (L == 0) return cudaSuccess;
     node_tables_kernel<<<L, kScanThreads, 0, st>>>(hex, L, ob, ze);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ (b + c)
-
-constexpr int kLwThreads = 256;
-constexpr int kLwItems = 16;                      // consecutive symbols per thread
-constexpr int kLwTile = kLwThreads * kLwItems;    // 4096 symbols = 8 rank blocks
-constexpr int kLwWarps = kLwThreads / 32;         // one warp = one 512-bit block
-static_assert(kLwItems * 32 == (int)kBlockBits, "a warp covers exactly one rank block");
-
-uint32_t lw_tile_elems() { return kLwTile; }
-
-struct LevelArgs {
-    const void *cur;
-    void *nxt;            // nullptr on the last level
-    uint64_t n;
-    uint64_t nblocks;
-    uint64_t nspans;
-    uint32_t L, l;
-    uint32_t ntiles;
-    LevelDesc lv;
-    uint64_t *ones_out;
-    const uint64_t *ob;   // level l's table (already offset)
-    const uint64_t *ze;
-    uint64_t *status;     // ntiles look-back words of this level
-    uint32_t *ticket;
-    uint32_t *err;
-};
-
-template <typename Sym>
-__device__ __forceinline__ void load_items(const Sym *__restrict__ src, uint64_t base, uint32_t p0, uint32_t cnt,
-                                           bool vec_ok, Sym (&v)[kLwItems]) {
-    if (vec_ok && p0 + kLwItems <= cnt) {
-        constexpr int kVec = kLwItems * sizeof(Sym) / 16;
-        const uint4 *q = reinterpret_cast<const uint4 *>(src + base + p0);
-        uint4 r[kVec];
-#pragma unroll
-        for (int k = 0; k < kVec; k++) r[k] = __ldcs(q + k);
-        const Sym *e = reinterpret_cast<const Sym *>(r);
-#pragma unroll
-        for (int k = 0; k < kLwItems; k++) v[k] = e[k];
-    } else {
-#pragma unroll
-        for (int k = 0; k < kLwItems; k++) v[k] = (p0 + k < cnt) ? src[base + p0 + k] : Sym(0);
-    }
-}
-
-template <typename Sym>
-__global__ void __launch_bounds__(kLwThreads) level_pass_kernel(LevelArgs a) {
-    __shared__ __align__(16) Sym s_split[kLwTile];
-    __shared__ uint32_t s_warp_excl[kLwWarps];
-    __shared__ uint64_t s_prefix;
-    __shared__ uint32_t s_tile, s_tile_ones;
-
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // A symbol-range fault found by the histogram (earlier on the stream)
-    // makes the node tables inconsistent with the data: skip the pass.
-    if (*(volatile uint32_t *)a.err & kErrSymbol) return;
-    if (t == 0) s_tile = atomicAdd(a.ticket, 1u);  // tiles in issue order: look-back waits only on earlier ones
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint64_t base = (uint64_t)tile * kLwTile;
-    const uint32_t cnt = (uint32_t)((a.n - base) < (uint64_t)kLwTile ? (a.n - base) : (uint64_t)kLwTile);
-    const uint32_t p0 = t * kLwItems;
-    const Sym *cur = static_cast<const Sym *>(a.cur);
-    const bool vec_ok = (reinterpret_cast<uintptr_t>(cur) & 15) == 0;
-
-    Sym v[kLwItems];
-    load_items<Sym>(cur, base, p0, cnt, vec_ok, v);
-
-    // Level-l bits of this thread's 16 symbols (bit k = symbol p0 + k).
-    const uint32_t sh = a.L - 1 - a.l;
-    uint32_t m = 0;
-#pragma unroll
-    for (int k = 0; k < kLwItems; k++) m |= (p0 + k < cnt ? ((uint32_t)v[k] >> sh) & 1u : 0u) << k;
-    const uint32_t c = __popc(m);
-
-    uint32_t inc = c;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += y;
-    }
-    const uint32_t lane_excl = inc - c;
-    if (lane == 31) s_warp_excl[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = lane < kLwWarps ? s_warp_excl[lane] : 0;
-        uint32_t winc = w;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, winc, d);
-            if (lane >= d) winc += y;
-        }
-        const uint32_t tile_ones = __shfl_sync(0xffffffffu, winc, kLwWarps - 1);
-        const uint64_t prefix = lookback_prefix(a.status, tile, tile_ones, a.err);
-        if (lane < kLwWarps) s_warp_excl[lane] = winc - w;
-        if (lane == 0) {
-            s_prefix = prefix;
-            s_tile_ones = tile_ones;
-        }
-    }
-    __syncthreads();
-    const uint64_t prefix = s_prefix;               // ones before this tile
-    const uint32_t tile_ones = s_tile_ones;
-    const uint32_t ones_before = s_warp_excl[warp] + lane_excl;  // inside the tile, before p0
-    const uint64_t gpos = base + p0;
-    const uint64_t block = gpos >> 9;
-
-    // Bitmap: 16 bits per thread, one coalesced 16-bit store (padding bits are 0).
-    if (block < a.nblocks) reinterpret_cast<uint16_t *>(a.lv.words)[gpos >> 4] = (uint16_t)m;
-
-    // Rank directory: lane 0 of each warp owns one 512-bit block.
-    if (lane == 0 && block < a.nblocks) {
-        const uint64_t before = prefix + s_warp_excl[warp];
-        a.lv.R[block] = (uint32_t)before;
-        if ((block & kBlocksPerSpanMask) == 0) a.lv.Hy[block >> (kSpanShift - 9)] = before;
-    }
-
-    // Select samples: a thread's 16 positions share one block, so a sample
-    // that falls among them is just that block.
-    const uint32_t valid = cnt > p0 ? (cnt - p0 < (uint32_t)kLwItems ? cnt - p0 : (uint32_t)kLwItems) : 0;
-    if (valid) {
-        const uint64_t g1 = prefix + ones_before;
-        const uint64_t k1 = ceil_div(g1, kSample);
-        if (k1 * kSample < g1 + c) a.lv.S1[k1] = (uint32_t)block;
-        const uint64_t g0 = gpos - g1;
-        const uint64_t k0 = ceil_div(g0, kSample);
-        if (k0 * kSample < g0 + (valid - c)) a.lv.S0[k0] = (uint32_t)block;
-    }
-
-    if (tile == a.ntiles - 1 && t == 0) {
-        const uint64_t total = prefix + tile_ones;
-        a.lv.R[a.nblocks] = (uint32_t)total;
-        a.lv.Hy[a.nspans] = total;
-        *a.ones_out = total;
-    }
-
-    if (a.nxt == nullptr) return;
-
-    // (c) Stable split of the tile by the level bit into shared memory
-    // (zeros first, then ones, order kept), then coalesced placement.
-    const uint32_t Zt = cnt - tile_ones;
-    uint32_t o = ones_before;
-#pragma unroll
-    for (int k = 0; k < kLwItems; k++) {
-        if (p0 + k < cnt) {
-            const uint32_t b = (m >> k) & 1u;
-            s_split[b ? Zt + o : p0 + k - o] = v[k];
-            o += b;
-        }
-    }
-    __syncthreads();
-    Sym *nxt = static_cast<Sym *>(a.nxt);
-    const uint64_t zeros_prefix = base - prefix;  // zeros before this tile
-    const uint32_t shv = a.L - a.l;               // key_l = s >> (L - l)
-    const uint32_t nodes = 1u << a.l;
-    bool bad = false;
-    for (uint32_t q = t; q < cnt; q += kLwThreads) {
-        const Sym s = s_split[q];
-        const uint32_t node = (uint32_t)s >> shv;
-        if (node >= nodes) {  // only after an earlier fault: never index past the tables
-            bad = true;
-            continue;
-        }
-        const uint64_t dst = q < Zt ? zeros_prefix + q + __ldg(a.ob + node)
-                                    : prefix + (q - Zt) + __ldg(a.ze + node);
-        if (dst < a.n)
-            nxt[dst] = s;
-        else
-            bad = true;
-    }
-    if (bad) atomicOr(a.err, kErrTimeout);
-}
-
-cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
-                              const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out,
-                              uint64_t *status, uint32_t *ticket, uint32_t *err, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    LevelArgs a;
-    a.cur = cur;
-    a.nxt = (l + 1 < L) ? nxt : nullptr;
-    a.n = n;
-    a.nblocks = ceil_div(n, kBlockBits);
-    a.nspans = ceil_div(n, 1ull << kSpanShift);
-    a.L = L;
-    a.l = l;
-    a.ntiles = (uint32_t)ceil_div(n, kLwTile);
-    a.lv = lv;
-    a.ones_out = ones_out;
-    a.ob = ob + ((1ull << l) - 1);
-    a.ze = ze + ((1ull << l) - 1);
-    a.status = status;
-    a.ticket = ticket;
-    a.err = err;
-    switch (width) {
-        case 1: level_pass_kernel<uint8_t><<<a.ntiles, kLwThreads, 0, st>>>(a); break;
-        case 2: level_pass_kernel<uint16_t><<<a.ntiles, kLwThreads, 0, st>>>(a); break;
-        case 4: level_pass_kernel<uint32_t><<<a.ntiles, kLwThreads, 0, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
     return cudaGetLastError();
 }
 

@@ -120,6 +120,144 @@ __device__ __forceinline__ uint64_t lookback_prefix(uint64_t *status, uint32_t t
     return excl;
 }
 
+// Publishes a tile's own count: the inclusive prefix for tile 0, else the
+// aggregate.  One lane.
+__device__ __forceinline__ void publish_aggregate(uint64_t *status, uint32_t tile, uint64_t agg) {
+    st_relaxed(&status[tile], (tile == 0 ? kFlagInc : kFlagAgg) | agg);
+}
+
+// Decoupled look-back with a 128-tile window, for a tile whose aggregate is
+// already published (publish_aggregate): each lane inspects four
+// predecessors per round, so the chain of inclusive prefixes advances 128
+// tiles per round trip to L2 instead of 32.  Returns the exclusive prefix and
+// publishes the inclusive one; bounded like lookback_prefix.
+__device__ __forceinline__ uint64_t lookback_published(uint64_t *status, uint32_t tile, uint64_t agg, uint32_t *err) {
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) return 0;
+    uint64_t excl = 0;
+    int64_t pos = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    bool gave_up = false;
+    while (true) {
+        uint64_t s[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t idx = pos - (4 * lane + j);
+            s[j] = idx >= 0 ? ld_relaxed(&status[idx]) : kFlagInc;
+        }
+        while (true) {
+            bool ready = true;
+#pragma unroll
+            for (int j = 0; j < 4; j++) ready &= (s[j] >> 62) != 0;
+            if (__all_sync(0xffffffffu, ready)) break;
+            // Give up after kMaxSpins polls, or at once when another CTA has
+            // already given up (its tiles may never be published).
+            if (++spins > kMaxSpins || ((spins & 255u) == 0 && (*(volatile uint32_t *)err & kErrTimeout))) {
+                gave_up = true;
+                break;
+            }
+            __nanosleep(32);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int64_t idx = pos - (4 * lane + j);
+                if ((s[j] >> 62) == 0) s[j] = ld_relaxed(&status[idx]);
+            }
+        }
+        if (gave_up) break;
+        int jfirst = 4;
+#pragma unroll
+        for (int j = 3; j >= 0; j--)
+            if ((s[j] >> 62) == 2) jfirst = j;
+        const uint32_t inc_lanes = __ballot_sync(0xffffffffu, jfirst < 4);
+        if (inc_lanes) {
+            const int L = __ffs(inc_lanes) - 1;
+            const int jl = __shfl_sync(0xffffffffu, jfirst, L);
+            uint64_t v = 0;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (lane < L || (lane == L && j <= jl)) v += s[j] & kValMask;
+            excl += warp_sum_u64(v);
+            break;
+        }
+        uint64_t v = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) v += s[j] & kValMask;
+        excl += warp_sum_u64(v);
+        pos -= 128;
+    }
+    if (gave_up && lane == 0) atomicOr(err, kErrTimeout);
+    if (lane == 0) st_relaxed(&status[tile], kFlagInc | (excl + agg));
+    return excl;
+}
+
+// ------------------------------------------------------- TMA + mbarrier
+// One-dimensional bulk copies global -> shared (cp.async.bulk) completing on
+// an mbarrier.  Every wait is bounded by kMaxSpins polls.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory
+// before later async-proxy (bulk copy) writes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Arms the barrier for `bytes` of transaction and issues the copy (bytes and
+// both addresses must be multiples of 16).
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Plain arrival (no transaction), for a phase with nothing to copy.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// A device-side wait gives up after this long (nanoseconds of %globaltimer).
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+// Waits for the barrier phase with parity `phase`; false if it gave up
+// (after kWaitLimitNs).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+    const uint32_t addr = smem_u32(bar);
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; i++) {
+        if ((i & 1023u) == 1023u && global_ns() - t0 > kWaitLimitNs) return false;
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------ launchers
 // (defined in build.cu / query.cu, called from abi.cu)
 
@@ -145,7 +283,7 @@ cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, ui
                                cudaStream_t st);
 
 // Kernels (b)+(c): one level pass.  status/tickets must be zeroed.
-uint32_t lw_tile_elems();
+uint32_t lw_tile_elems(int width);
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out,
                               uint64_t *status, uint32_t *ticket, uint32_t *err, cudaStream_t st);

@@ -121,3 +121,15 @@ def test_async_build_on_stream_and_torch_allocator():
         t.free()
     finally:
         W.use_torch_allocator(False)
+
+
+@pytest.mark.parametrize("sigma,dtype,log2n,alpha", [(96, np.uint8, 25, 1.0), (4, np.uint8, 25, 0.0),
+                                                     (65536, np.uint16, 23, 1.1), (1 << 20, np.uint32, 22, 1.2)])
+def test_many_tiles_per_cta_pipeline(sigma, dtype, log2n, alpha):
+    """Enough tiles that every persistent CTA streams several (the producer /
+    compute pipeline runs at full depth), plus a ragged tail."""
+    W = wt()
+    n = (1 << log2n) + 777
+    S = inputs.zipf(n, sigma, alpha, 4242, dtype) if alpha else inputs.uniform(n, sigma, 4242, dtype)
+    t = W.Tree.build(to_dev(S), sigma)
+    compare_tree(t, S, sigma)
