@@ -209,6 +209,33 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
                         const uint64_t *Hex, uint32_t *words, uint32_t *R, void *nxt, void *stream);
 
 /*
+ * wt_node_starts_noalloc: the same result as wt_node_starts (Hex, 2^L + 1
+ * uint64 node starts written to the device array Hex) for callers that may
+ * not allocate device memory while they run -- for example a process that
+ * gives the whole device to its own memory pool at start-up, or a loop that
+ * must not take the allocator's locks or the synchronisation a free can
+ * bring.  The paper has no counterpart; it is a deployment variant.
+ *
+ * It allocates nothing: its scratch (the per-code counts and an error word)
+ * is one fixed array of about 0.5 MB compiled into the library, present on
+ * every GPU that loads the library until the process exits.  Limits and
+ * behaviour:
+ *   - sigma must be at most 65536 (2^16); larger alphabets give WT_ERR_ARG
+ *     (use wt_node_starts for them).  S must be device memory.
+ *   - The first call on a device looks up the array's device address on
+ *     that device (with it current); make that first call before any stream
+ *     capture.
+ *   - Every call shares the one array and clears the part it uses before
+ *     use; calls that overlap on the GPU (concurrent streams, threads or
+ *     devices sharing a context) race on it and must be serialised by the
+ *     caller.
+ *   - Synchronous: returns after its stream has finished, with
+ *     WT_ERR_SYMBOL_RANGE if some symbol is >= sigma.
+ */
+wt_status wt_node_starts_noalloc(const void *S, uint64_t n, uint64_t sigma, int sym_width, uint64_t *Hex,
+                                 void *stream);
+
+/*
  * Per-kernel timing (no counterpart in the paper; it times the hot path).
  * Between wt_profile_begin and wt_profile_end every kernel launch of the
  * library is bracketed by CUDA events on the stream it runs on.

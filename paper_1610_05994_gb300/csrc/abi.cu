@@ -411,6 +411,11 @@ wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int 
 
 }  // namespace
 
+namespace wt {
+// Sets the calling thread's last status (for entry points in other files).
+wt_status record_status(wt_status s) { return set_last(s); }
+}  // namespace wt
+
 // ====================================================================== ABI
 
 extern "C" {

@@ -73,6 +73,7 @@ _SIGNATURES = [
     ("wt_node_starts", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     ("wt_level_step", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_uint32, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("wt_node_starts_noalloc", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     ("wt_profile_begin", C.c_int, []),
     ("wt_profile_end", C.c_int, [C.POINTER(_KernelStat), C.c_uint32, C.POINTER(C.c_uint32)]),
 ]
@@ -304,6 +305,18 @@ def node_starts(S: torch.Tensor, sigma: int, stream=None) -> torch.Tensor:
     hex_ = torch.empty((1 << L) + 1, dtype=torch.uint64, device=S.device)
     _check(load().wt_node_starts(C.c_void_p(_dptr(S)), S.numel(), sigma, S.element_size(),
                                  C.c_void_p(_dptr(hex_)), C.c_void_p(_stream(stream))), "wt_node_starts")
+    return hex_
+
+
+def node_starts_noalloc(S: torch.Tensor, sigma: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Hex like node_starts, through the entry point that allocates no device
+    memory (scratch in a fixed library array; sigma <= 2^16; calls must not
+    overlap on the GPU)."""
+    L = max(0, (sigma - 1).bit_length())
+    hex_ = torch.empty((1 << L) + 1, dtype=torch.uint64, device=S.device) if out is None else out
+    _check(load().wt_node_starts_noalloc(C.c_void_p(_dptr(S)), S.numel(), sigma, S.element_size(),
+                                         C.c_void_p(_dptr(hex_)), C.c_void_p(_stream(stream))),
+           "wt_node_starts_noalloc")
     return hex_
 
 
