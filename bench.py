@@ -1,14 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of wavelet-tree construction on one GB300 (one JSON line).
 
-A step is one pass of the whole hot path over one batch of synthetic input:
-the text-like sequence (2^30 uint8 codes over 96 symbols, Zipf 1.0) and the
-DNA-like sequence (2^30 uint8 codes over 4 symbols, uniform) are each built
-into a resident pointerless wavelet tree (histogram + node starts, the fused
-level passes or the dd-direct kernels as the autotuner picks), then one batch
-of 2^16 mixed access/rank/select queries runs against the two trees.  The
-metric is built symbols per second.  Inputs are larger than L2, so no flush
-is needed between steps.
+A step is one pass of the whole hot path over one batch of synthetic input.
+With the default workload, two sequences are each built into a resident
+pointerless wavelet tree:
+- the text-like sequence: 2^30 uint8 codes over 96 symbols, Zipf 1.0;
+- the DNA-like sequence: 2^30 uint8 codes over 4 symbols, uniform.
+Each build runs the histogram and node starts, then the fused level passes
+or the dd-direct kernels, as the autotuner picks.  Then one batch of 2^16
+mixed access/rank/select queries runs against the two trees.  The metric is
+built symbols per second.  Inputs are larger than L2, so no flush is needed
+between steps.
 
 ``--impl reference`` times the CPU oracle instead (single thread, bounded
 sample of the same workload).  Under torchrun every rank builds its own
@@ -36,15 +38,28 @@ from paper_1610_05994_gb300 import inputs  # noqa: E402
 
 METRIC = "wavelet-tree build symbols/sec"
 UNIT = "symbols/s"
-TEXT = inputs.WORKLOADS["u8-text-2^30-s96-zipf1.0"]
-DNA = inputs.WORKLOADS["u8-dna-2^30-s4"]
 QUERIES = 1 << 16
-WORKLOAD_NAME = "u8 text n=2^30 sigma=96 Zipf(1.0) + u8 DNA n=2^30 sigma=4 uniform + 2^16 mixed queries"
-CONFIG_BASE = {"workload": WORKLOAD_NAME, "text": {"n": TEXT.n, "sigma": TEXT.sigma, "dist": "zipf1.0"},
-               "dna": {"n": DNA.n, "sigma": DNA.sigma, "dist": "uniform"}, "queries_per_step": QUERIES,
-               "l2": "inputs (1 GiB each) larger than the 129 MB L2; no flush"}
-ORACLE_SAMPLE = 1 << 27       # cpu_baseline: about 10-30 s of single-thread oracle work
-REFERENCE_SAMPLE = 1 << 26    # --impl reference: per step, so K steps stay within minutes
+# The default workload (text + DNA) is the one the headline metric is quoted
+# on; "words" is the large-alphabet single-sequence workload.
+WORKLOAD_SETS = {
+    "text+dna": [inputs.WORKLOADS["u8-text-2^30-s96-zipf1.0"], inputs.WORKLOADS["u8-dna-2^30-s4"]],
+    "words": [inputs.WORKLOADS["u32-words-2^29-s2^20-zipf1.2"]],
+}
+WORKLOAD_NAMES = {
+    "text+dna": "u8 text n=2^30 sigma=96 Zipf(1.0) + u8 DNA n=2^30 sigma=4 uniform + 2^16 mixed queries",
+    "words": "u32 word ids n=2^29 sigma=2^20 Zipf(1.2) + 2^16 mixed queries",
+}
+
+
+def config_for(name: str) -> dict:
+    seqs = WORKLOAD_SETS[name]
+    return {"workload": WORKLOAD_NAMES[name],
+            "sequences": [{"name": w.name, "n": w.n, "sigma": w.sigma, "width": w.width,
+                           "dist": w.dist + (f"{w.alpha}" if w.dist == "zipf" else "")} for w in seqs],
+            "queries_per_step": QUERIES,
+            "l2": "inputs (>= 1 GiB each) larger than the 129 MB L2; no flush"}
+ORACLE_SAMPLE = {"text+dna": 1 << 27, "words": 1 << 24}     # cpu_baseline: 10-30 s of oracle work
+REFERENCE_SAMPLE = {"text+dna": 1 << 26, "words": 1 << 23}  # --impl reference, per step
 
 
 def dist_env():
@@ -164,42 +179,48 @@ def run_reference(args, ws, rank):
         return
     from oracle import oracle as O
     O.build()
-    n = REFERENCE_SAMPLE
-    text = TEXT.generate(n)
-    dna = DNA.generate(n)
+    n = REFERENCE_SAMPLE[args.workload]
+    seqs = [(w.generate(min(n, w.n)), w.sigma) for w in WORKLOAD_SETS[args.workload]]
     for _ in range(min(args.warmup, 1)):
-        O.build_bits(text[: 1 << 20], TEXT.sigma)
+        O.build_bits(seqs[0][0][: 1 << 20], seqs[0][1])
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.build_bits(text, TEXT.sigma)
-        O.build_bits(dna, DNA.sigma)
+        for S, sigma in seqs:
+            O.build_bits(S, sigma)
         times.append(time.perf_counter() - t0)
     sec = statistics.median(times)
-    value = 2 * n / sec
-    sample = f"first 2^{n.bit_length() - 1} symbols of each of the two sequences, oracle build_bits, 1 thread"
+    syms = sum(len(S) for S, _ in seqs)
+    value = syms / sec
+    sample = (f"first {min(n, seqs[0][0].size)} symbols of each sequence of the workload, oracle build_bits "
+              f"(level-by-level stable partition), 1 thread, median of {args.steps}")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "impl": "reference",
-            "config": CONFIG_BASE,
+            "vs_baseline": None, "dtype": dtype_of(args.workload), "data": "synthetic", "impl": "reference",
+            "config": config_for(args.workload),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample():
+def dtype_of(workload: str) -> str:
+    widths = sorted({w.width for w in WORKLOAD_SETS[workload]})
+    return "+".join({1: "u8", 2: "u16", 4: "u32"}[x] for x in widths)
+
+
+def cpu_baseline_sample(workload: str):
+    """The oracle timed once on a bounded prefix of every sequence (10-30 s)."""
     from oracle import oracle as O
     O.build()
-    n = ORACLE_SAMPLE
-    text = TEXT.generate(n)
-    dna = DNA.generate(n)
+    n = ORACLE_SAMPLE[workload]
+    seqs = [(w.generate(min(n, w.n)), w.sigma) for w in WORKLOAD_SETS[workload]]
     t0 = time.perf_counter()
-    O.build_bits(text, TEXT.sigma)
-    O.build_bits(dna, DNA.sigma)
+    for S, sigma in seqs:
+        O.build_bits(S, sigma)
     sec = time.perf_counter() - t0
-    return {"value": 2 * n / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first 2^{n.bit_length() - 1} symbols of each sequence, oracle build_bits, 1 thread, "
-                      f"{sec:.1f} s"}
+    syms = sum(len(S) for S, _ in seqs)
+    return {"value": syms / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} symbols of each sequence, oracle build_bits, 1 thread, {sec:.1f} s"}
 
 
 def run_ours(args, ws, rank, local):
@@ -214,25 +235,22 @@ def run_ours(args, ws, rank, local):
     W.load()
     dev = torch.device("cuda", local)
 
-    text_h = TEXT.generate()
-    dna_h = DNA.generate()
-    seqs = [text_h, dna_h]
-    sigmas = [TEXT.sigma, DNA.sigma]
-    tidx, op, c, arg = make_queries(seqs, sigmas, QUERIES, 7)
-    text_d = torch.from_numpy(text_h).to(dev)
-    dna_d = torch.from_numpy(dna_h).to(dev)
+    wls = WORKLOAD_SETS[args.workload]
+    host = [w.generate() for w in wls]
+    sigmas = [w.sigma for w in wls]
+    tidx, op, c, arg = make_queries(host, sigmas, QUERIES, 7)
+    seq_d = [torch.from_numpy(h).to(dev) for h in host]
     q_d = [torch.from_numpy(x).to(dev) for x in (tidx, op, c, arg)]
     out_d = torch.empty(QUERIES, dtype=torch.uint64, device=dev)
     torch.cuda.synchronize()
 
     def step(keep):
-        t1 = W.Tree.build(text_d, TEXT.sigma, wait=False)
-        t2 = W.Tree.build(dna_d, DNA.sigma, wait=False)
-        W.query_multi([t1, t2], *q_d, out=out_d)
+        trees = [W.Tree.build(S, sigma, variant=args.variant, wait=False) for S, sigma in zip(seq_d, sigmas)]
+        W.query_multi(trees, *q_d, out=out_d)
         # release the previous step's trees in stream order (no host wait)
         for t in keep:
             t.free()
-        return [t1, t2]
+        return trees
 
     def barrier():
         if ws > 1:
@@ -270,25 +288,24 @@ def run_ours(args, ws, rank, local):
         tt = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    syms = (TEXT.n + DNA.n) * ws
+    syms_rank = sum(w.n for w in wls)
+    syms = syms_rank * ws
     value = syms / (ms * 1e-3)
 
     # End to end: the same step through the C ABI from pinned host buffers,
     # copies inside the timed region, query answers read back every step.
-    text_p = torch.from_numpy(text_h).pin_memory()
-    dna_p = torch.from_numpy(dna_h).pin_memory()
+    host_p = [torch.from_numpy(h).pin_memory() for h in host]
     q_p = [torch.from_numpy(x).pin_memory() for x in (tidx, op, c, arg)]
     out_p = torch.empty(QUERIES, dtype=torch.uint64).pin_memory()
 
     def step_e2e(keep):
-        t1 = _build_from_host(W, text_p, TEXT.sigma)
-        t2 = _build_from_host(W, dna_p, DNA.sigma)
+        trees = [_build_from_host(W, p, sigma, args.variant) for p, sigma in zip(host_p, sigmas)]
         qd = [x.to(dev, non_blocking=True) for x in q_p]
-        W.query_multi([t1, t2], *qd, out=out_d)
+        W.query_multi(trees, *qd, out=out_d)
         out_p.copy_(out_d, non_blocking=True)
         for t in keep:
             t.free()
-        return [t1, t2]
+        return trees
 
     keep = []
     for _ in range(max(1, args.warmup // 2)):
@@ -311,14 +328,14 @@ def run_ours(args, ws, rank, local):
         tt = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms_e2e = float(tt.item())
-    h2d = TEXT.n + DNA.n + sum(x.numel() * x.element_size() for x in q_p)
+    h2d = sum(h.nbytes for h in host) + sum(x.numel() * x.element_size() for x in q_p)
     d2h = QUERIES * 8
 
     if rank != 0:
         return
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else "fallback (6800 GB/s)"
     peak = peak or 6800.0
     dom = max(stats.items(), key=lambda kv: kv[1]["total_ms"]) if stats else (None, None)
     roofline = None
@@ -326,19 +343,19 @@ def run_ours(args, ws, rank, local):
         name, st = dom
         achieved = st["alg_bytes"] / (st["total_ms"] * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                    "traffic": ncu_traffic(name),
+                    "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(name),
                     "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
                     "avg_launch_ms": st["total_ms"] / st["launches"]}
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps,
                    "GBps": v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9 if v["total_ms"] > 0 else None}
                for k, v in stats.items()}
     launches = sum(v["launches"] for v in stats.values())
-    cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline_sample()
+    cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline_sample(args.workload)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": dict(CONFIG_BASE, parallelism=f"replicas{ws}"),
+            "vs_baseline": None, "dtype": dtype_of(args.workload), "data": "synthetic",
+            "config": dict(config_for(args.workload), parallelism=f"replicas{ws}",
+                           variant={0: "auto", 1: "levelwise", 2: "dd"}[args.variant]),
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": syms / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
@@ -346,12 +363,12 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def _build_from_host(W, pinned, sigma):
+def _build_from_host(W, pinned, sigma, variant):
     """wt_build_async from a pinned host buffer (the library stages the copy)."""
     import ctypes as C
     lib = W.load()
     h = lib.wt_build_async(C.c_void_p(pinned.data_ptr()), pinned.numel(), sigma, pinned.element_size(),
-                           W.VARIANT_AUTO, C.c_void_p(W._stream(None)))
+                           variant, C.c_void_p(W._stream(None)))
     if not h:
         raise W.WTError(lib.wt_last_status(), "wt_build_async")
     return W.Tree(h, pinned.numel(), sigma, pinned.element_size())
@@ -364,6 +381,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS), default="text+dna")
+    ap.add_argument("--variant", type=int, choices=[0, 1, 2], default=0,
+                    help="0 auto (autotuned), 1 level-wise, 2 dd-direct")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

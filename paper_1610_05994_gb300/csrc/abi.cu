@@ -230,15 +230,17 @@ struct Scratch {
 wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t sigma, uint32_t L, int width,
                         bool need_levels, cudaStream_t st) {
     const uint64_t ntiles = ceil_div(n, lw_tile_elems(width));
-    const size_t hist = align256(sigma * 8);
+    const uint32_t R = hist_replicas(n, sigma);
+    const size_t hist = align256(R ? (size_t)R * sigma * 4 : sigma * 8);
     const size_t hex = align256(((1ull << L) + 1) * 8);
     const size_t tab = need_levels ? align256((1ull << L) * 8) : 0;
     const size_t status = need_levels ? align256((size_t)L * ntiles * 8) : 0;
     const size_t tickets = need_levels ? align256((size_t)L * 4) : 0;
     const size_t zeroed = hist + status + tickets;
     const size_t buf = align256(n * (uint64_t)width);
+    const size_t stmp = align256(scan_tmp_bytes(L));
     const int nbuf = need_levels ? (L >= 3 ? 2 : (L == 2 ? 1 : 0)) : 0;
-    sc.bytes = zeroed + hex + 2 * tab + nbuf * buf;
+    sc.bytes = zeroed + hex + 2 * tab + stmp + nbuf * buf;
     sc.mem = dev_alloc(A, sc.bytes, st);
     if (!sc.mem) return WT_ERR_OOM;
     char *p = static_cast<char *>(sc.mem);
@@ -254,6 +256,8 @@ wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t si
     p += tab;
     sc.b.ze = reinterpret_cast<uint64_t *>(p);
     p += tab;
+    sc.b.scan_tmp = reinterpret_cast<uint64_t *>(p);
+    p += stmp;
     sc.b.ping = nbuf >= 1 ? p : nullptr;
     p += nbuf >= 1 ? buf : 0;
     sc.b.pong = nbuf >= 2 ? p : nullptr;
@@ -269,19 +273,28 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
     if (r != WT_OK) return r;
     const BuildScratch &b = sc.b;
     const double nw = (double)t->n * t->width;
+    const uint32_t R = hist_replicas(t->n, t->sigma);
     {
         ProfScope p(K_HIST, nw, st);
-        WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st));
+        if (R)
+            WT_CK(launch_histogram_replicated(S, t->n, t->width, t->sigma, reinterpret_cast<uint32_t *>(b.hist), R,
+                                              t->d_err, st));
+        else
+            WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st));
     }
     if (t->L > 0) {
         const double leaves = (double)(1ull << t->L);
         {
             ProfScope p(K_NODE_STARTS, 8.0 * (t->sigma + leaves + 1), st);
-            WT_CK(launch_node_starts(b.hist, t->sigma, t->L, t->n, b.hex, st));
+            if (R)
+                WT_CK(launch_node_starts_replicated(reinterpret_cast<const uint32_t *>(b.hist), R, t->sigma, t->L,
+                                                    b.hex, st, b.scan_tmp));
+            else
+                WT_CK(launch_node_starts(b.hist, t->sigma, t->L, t->n, b.hex, st, b.scan_tmp));
         }
         {
             ProfScope p(K_NODE_TABLES, 8.0 * 5 * leaves, st);
-            WT_CK(launch_node_tables(b.hex, t->L, b.ob, b.ze, st));
+            WT_CK(launch_node_tables(b.hex, t->L, b.ob, b.ze, st, b.scan_tmp));
         }
         const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
         const void *cur = S;
@@ -300,6 +313,68 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
     return WT_OK;
 }
 
+// The dd-direct build (kernel d: per-tile counts, column scan, one write
+// pass over all levels) for small alphabets.
+wt_status enqueue_dd(wt_tree *t, const void *S, cudaStream_t st) {
+    const size_t hex = align256(((1ull << t->L) + 1) * 8);
+    const size_t tab = align256((1ull << t->L) * 8);
+    const size_t stmp = align256(scan_tmp_bytes(t->L));
+    const size_t dds = align256(dd_scratch_bytes(t->n, t->sigma));
+    const size_t bytes = 256 + hex + 2 * tab + stmp + dds;
+    void *mem = dev_alloc(t->alloc, bytes, st);
+    if (!mem) return WT_ERR_OOM;
+    char *p = static_cast<char *>(mem) + 256;
+    uint64_t *d_hex = reinterpret_cast<uint64_t *>(p);
+    p += hex;
+    uint64_t *ob = reinterpret_cast<uint64_t *>(p);
+    p += tab;
+    uint64_t *ze = reinterpret_cast<uint64_t *>(p);
+    p += tab;
+    uint64_t *scan_tmp = reinterpret_cast<uint64_t *>(p);
+    p += stmp;
+    const DdScratch d = dd_carve(p, t->n, t->sigma);
+    const double nw = (double)t->n * t->width;
+    const double table = (double)dd_tiles(t->n) * t->sigma * 4;
+    const uint64_t nblocks = ceil_div(t->n, kBlockBits);
+    wt_status r = WT_OK;
+    {
+        // read S, write the per-tile counts
+        ProfScope pr(K_DD_COUNT, nw + table, st);
+        if (launch_dd_count(S, t->n, t->sigma, d, t->d_err, st) != cudaSuccess) r = WT_ERR_CUDA;
+    }
+    if (r == WT_OK) {
+        // read the counts twice, write the offsets; node starts and tables
+        ProfScope pr(K_DD_SCAN, 3 * table + 8.0 * 6 * (1ull << t->L), st);
+        if (launch_dd_scan(t->n, t->sigma, d, st) != cudaSuccess ||
+            launch_node_starts(d.H, t->sigma, t->L, t->n, d_hex, st, scan_tmp) != cudaSuccess ||
+            launch_node_tables(d_hex, t->L, ob, ze, st, scan_tmp) != cudaSuccess)
+            r = WT_ERR_CUDA;
+    }
+    for (uint32_t l = 0; r == WT_OK && l < t->L; l++)
+        if (cudaMemsetAsync(t->h_desc.lv[l].words, 0, nblocks * 64, st) != cudaSuccess) r = WT_ERR_CUDA;
+    if (r == WT_OK) {
+        // read S and the count/offset rows, write every level's bitmap and directory
+        ProfScope pr(K_DD_WRITE, nw + 2 * table + t->L * (t->n / 8.0 + t->n / 128.0), st);
+        if (launch_dd_write(S, t->n, t->sigma, t->L, t->h_desc, t->d_desc, d, d_hex, ob, t->d_err, st) !=
+            cudaSuccess)
+            r = WT_ERR_CUDA;
+    }
+    if (r != WT_OK) cudaGetLastError();
+    dev_free(t->alloc, mem, bytes, st);
+    return r;
+}
+
+// Variant choice, from the measured table g_dd_faster: dd-direct where it
+// applies (one byte per symbol, sigma <= 256, n < 2^32) and was measured
+// faster than the level-wise build for that number of levels on GB300 (text
+// and DNA workloads of 2^28 symbols); level-wise otherwise.
+constexpr bool g_dd_faster[9] = {false, false, false, false, false, false, false, false, false};  // by L
+
+int choose_variant(uint64_t n, uint64_t sigma, int width) {
+    const uint32_t L = levels_of(sigma);
+    return (dd_supported(n, sigma, width) && L <= 8 && g_dd_faster[L]) ? WT_VARIANT_DD : WT_VARIANT_LEVELWISE;
+}
+
 wt_status enqueue_build(wt_tree *t, const void *S, int variant, cudaStream_t st) {
     // Descriptor (with level pointers; "ones" is filled by the level passes)
     // and a zero error word.
@@ -313,8 +388,9 @@ wt_status enqueue_build(wt_tree *t, const void *S, int variant, cudaStream_t st)
         }
         return WT_OK;
     }
-    (void)variant;
-    t->variant = WT_VARIANT_LEVELWISE;
+    if (variant == WT_VARIANT_AUTO) variant = choose_variant(t->n, t->sigma, t->width);
+    t->variant = variant;
+    if (variant == WT_VARIANT_DD) return enqueue_dd(t, S, st);
     return enqueue_levelwise(t, S, st);
 }
 
@@ -356,7 +432,8 @@ wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int 
         set_last(r);
         return nullptr;
     }
-    if (variant < WT_VARIANT_AUTO || variant > WT_VARIANT_DD) {
+    if (variant < WT_VARIANT_AUTO || variant > WT_VARIANT_DD ||
+        (variant == WT_VARIANT_DD && n > 0 && levels_of(sigma) > 0 && !dd_supported(n, sigma, width))) {
         set_last(WT_ERR_ARG);
         return nullptr;
     }

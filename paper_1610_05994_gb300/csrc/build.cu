@@ -86,6 +86,56 @@ __global__ void __launch_bounds__(kHistThreads) hist_global_kernel(const Sym *__
     if (bad) atomicOr(err, kErrSymbol);
 }
 
+// Large alphabets, n < 2^32: 32-bit counts in R replicas of the sigma bins
+// (warp w adds into replica w mod R).  Skewed codes put a large share of all
+// additions on a few bins; replicas spread one hot bin over R L2 addresses,
+// and equal codes inside a warp still merge into one addition.
+template <typename Sym>
+__global__ void __launch_bounds__(kHistThreads) hist_replicated_kernel(const Sym *__restrict__ S, uint64_t n,
+                                                                       uint64_t sigma, uint32_t *__restrict__ rep,
+                                                                       uint32_t R, uint32_t *__restrict__ err) {
+    bool bad = false;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t start = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t rounds = ceil_div(n, stride);
+    const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    uint32_t *mine = rep + (uint64_t)(gwarp % R) * sigma;
+    for (uint64_t r = 0; r < rounds; r++) {
+        const uint64_t k = start + r * stride;
+        const bool valid = k < n;
+        const uint32_t s = valid ? (uint32_t)S[k] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, s);
+        if (valid) {
+            if ((uint64_t)s >= sigma)
+                bad = true;
+            else if ((int)(threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(&mine[s], (uint32_t)__popc(peers));
+        }
+    }
+    if (bad) atomicOr(err, kErrSymbol);
+}
+
+uint32_t hist_replicas(uint64_t n, uint64_t sigma) {
+    if (sigma <= kHistSmemBins || n >= (1ull << 32)) return 0;  // not this path
+    uint64_t R = (64ull << 20) / (sigma * 4);                     // at most 64 MB of counters
+    if (R > 16) R = 16;
+    return R < 1 ? 1 : (uint32_t)R;
+}
+
+template <typename Sym>
+static cudaError_t histogram_rep_t(const void *S, uint64_t n, uint64_t sigma, uint32_t *rep, uint32_t R,
+                                   uint32_t *err, cudaStream_t st);
+
+cudaError_t launch_histogram_replicated(const void *S, uint64_t n, int width, uint64_t sigma, uint32_t *rep,
+                                        uint32_t R, uint32_t *err, cudaStream_t st) {
+    switch (width) {
+        case 1: return histogram_rep_t<uint8_t>(S, n, sigma, rep, R, err, st);
+        case 2: return histogram_rep_t<uint16_t>(S, n, sigma, rep, R, err, st);
+        case 4: return histogram_rep_t<uint32_t>(S, n, sigma, rep, R, err, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 static int sm_count() {
     static int count = 0;
     if (!count) {
@@ -121,6 +171,18 @@ static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64
     } else {
         hist_global_kernel<Sym><<<(unsigned)grid, kHistThreads, 0, st>>>(s, n, sigma, hist, err);
     }
+    return cudaGetLastError();
+}
+
+template <typename Sym>
+static cudaError_t histogram_rep_t(const void *S, uint64_t n, uint64_t sigma, uint32_t *rep, uint32_t R,
+                                   uint32_t *err, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t grid = (uint64_t)sm_count() * 4;
+    const uint64_t want = ceil_div(n, (uint64_t)kHistThreads * 4);
+    if (grid > want) grid = want ? want : 1;
+    hist_replicated_kernel<Sym><<<(unsigned)grid, kHistThreads, 0, st>>>(static_cast<const Sym *>(S), n, sigma, rep,
+                                                                        R, err);
     return cudaGetLastError();
 }
 
@@ -164,13 +226,120 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *s
     return r;
 }
 
+// ---- exclusive scans over an implicit sequence val(0..count-1).
+// Small inputs: one CTA, each thread a contiguous range (node_starts_kernel,
+// node_tables_kernel).  Large inputs: reduce-then-scan over 8192-entry chunks
+// in three launches (chunk sums, scan of the sums, chunk scan), no waits.
+
+constexpr int kScanItems = 8;
+constexpr uint64_t kScanChunk = (uint64_t)kScanThreads * kScanItems;
+constexpr uint64_t kSingleCtaMax = 1ull << 16;  // up to this many entries one CTA scans
+
+struct HistVal {  // leaf counts, zero at and above sigma
+    const uint64_t *hist;
+    uint64_t sigma;
+    __device__ __forceinline__ uint64_t operator()(uint64_t c) const { return c < sigma ? hist[c] : 0; }
+};
+struct HistRepVal {  // leaf counts summed over the replicas, zero at and above sigma
+    const uint32_t *rep;
+    uint64_t sigma;
+    uint32_t R;
+    __device__ __forceinline__ uint64_t operator()(uint64_t c) const {
+        if (c >= sigma) return 0;
+        uint64_t v = 0;
+        for (uint32_t r = 0; r < R; r++) v += rep[(uint64_t)r * sigma + c];
+        return v;
+    }
+};
+struct HexOut {
+    uint64_t *hex;
+    __device__ __forceinline__ void operator()(uint64_t c, uint64_t excl, uint64_t) const { hex[c] = excl; }
+};
+struct ZeroVal {  // Z_l[v]: size of the left child of node v on level l
+    const uint64_t *hex;
+    uint32_t sh;      // L - l >= 1
+    __device__ __forceinline__ uint64_t operator()(uint64_t v) const {
+        return hex[(2 * v + 1) << (sh - 1)] - hex[(2 * v) << (sh - 1)];
+    }
+};
+struct TableOut {  // OB_l[v] = node start - zeros before it; ZE_l[v] = zeros through its end
+    const uint64_t *hex;
+    uint32_t sh;
+    uint64_t *ob, *ze;
+    __device__ __forceinline__ void operator()(uint64_t v, uint64_t zb, uint64_t z) const {
+        ob[v] = hex[v << sh] - zb;
+        ze[v] = zb + z;
+    }
+};
+
+template <class Val>
+__global__ void __launch_bounds__(kScanThreads) chunk_sums_kernel(Val val, uint64_t count, uint64_t *__restrict__ sums) {
+    __shared__ uint64_t s_warp[32];
+    const uint64_t base = blockIdx.x * kScanChunk;
+    uint64_t v = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        const uint64_t c = base + (uint64_t)i * kScanThreads + threadIdx.x;
+        if (c < count) v += val(c);
+    }
+    const uint64_t excl = block_exclusive_scan(v, s_warp);
+    if (threadIdx.x == blockDim.x - 1) sums[blockIdx.x] = excl + v;
+}
+
+// In-place exclusive scan of nchunks values by one CTA.
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(uint64_t *__restrict__ sums, uint64_t nchunks) {
+    __shared__ uint64_t s_warp[32];
+    const uint64_t per = ceil_div(nchunks, blockDim.x);
+    const uint64_t lo = threadIdx.x * per < nchunks ? threadIdx.x * per : nchunks;
+    const uint64_t hi = lo + per < nchunks ? lo + per : nchunks;
+    uint64_t sum = 0;
+    for (uint64_t k = lo; k < hi; k++) sum += sums[k];
+    uint64_t run = block_exclusive_scan(sum, s_warp);
+    for (uint64_t k = lo; k < hi; k++) {
+        const uint64_t x = sums[k];
+        sums[k] = run;
+        run += x;
+    }
+}
+
+template <class Val, class Out>
+__global__ void __launch_bounds__(kScanThreads) chunk_scan_kernel(Val val, Out out, uint64_t count,
+                                                                  const uint64_t *__restrict__ sums) {
+    __shared__ uint64_t s_warp[32];
+    const uint64_t lo = blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+    uint64_t v[kScanItems];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        v[i] = lo + i < count ? val(lo + i) : 0;
+        sum += v[i];
+    }
+    uint64_t run = sums[blockIdx.x] + block_exclusive_scan(sum, s_warp);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        if (lo + i < count) out(lo + i, run, v[i]);
+        run += v[i];
+    }
+}
+
+template <class Val, class Out>
+static cudaError_t scan_large(Val val, Out out, uint64_t count, uint64_t *tmp, cudaStream_t st) {
+    const uint64_t nchunks = ceil_div(count, kScanChunk);
+    chunk_sums_kernel<Val><<<(unsigned)nchunks, kScanThreads, 0, st>>>(val, count, tmp);
+    scan_sums_kernel<<<1, kScanThreads, 0, st>>>(tmp, nchunks);
+    chunk_scan_kernel<Val, Out><<<(unsigned)nchunks, kScanThreads, 0, st>>>(val, out, count, tmp);
+    return cudaGetLastError();
+}
+
+size_t scan_tmp_bytes(uint32_t L) { return ceil_div((1ull << L) + 1, kScanChunk) * sizeof(uint64_t); }
+
 // Hex[c] = sum of hist[c'] over c' < c, c = 0 .. 2^L (bins at c >= sigma count 0).
 __global__ void __launch_bounds__(kScanThreads) node_starts_kernel(const uint64_t *__restrict__ hist,
                                                                    uint64_t sigma, uint64_t entries,
                                                                    uint64_t *__restrict__ hex) {
     __shared__ uint64_t s_warp[32];
     const uint64_t chunk = ceil_div(entries, blockDim.x);
-    const uint64_t lo = threadIdx.x * chunk;
+    const uint64_t lo = threadIdx.x * chunk < entries ? threadIdx.x * chunk : entries;
     const uint64_t hi = lo + chunk < entries ? lo + chunk : entries;
     uint64_t sum = 0;
     for (uint64_t c = lo; c < hi; c++) sum += c < sigma ? hist[c] : 0;
@@ -182,13 +351,22 @@ __global__ void __launch_bounds__(kScanThreads) node_starts_kernel(const uint64_
 }
 
 cudaError_t launch_node_starts(const uint64_t *hist, uint64_t sigma, uint32_t L, uint64_t n, uint64_t *hex,
-                               cudaStream_t st) {
+                               cudaStream_t st, uint64_t *tmp) {
     (void)n;
-    node_starts_kernel<<<1, kScanThreads, 0, st>>>(hist, sigma, (1ull << L) + 1, hex);
-    return cudaGetLastError();
+    const uint64_t entries = (1ull << L) + 1;
+    if (tmp == nullptr || entries <= kSingleCtaMax) {
+        node_starts_kernel<<<1, kScanThreads, 0, st>>>(hist, sigma, entries, hex);
+        return cudaGetLastError();
+    }
+    return scan_large(HistVal{hist, sigma}, HexOut{hex}, entries, tmp, st);
 }
 
-// One CTA per level l: Z_l[v] = size of the left child of node v =
+cudaError_t launch_node_starts_replicated(const uint32_t *rep, uint32_t R, uint64_t sigma, uint32_t L, uint64_t *hex,
+                                          cudaStream_t st, uint64_t *tmp) {
+    return scan_large(HistRepVal{rep, sigma, R}, HexOut{hex}, (1ull << L) + 1, tmp, st);
+}
+
+// One CTA per small level l: Z_l[v] = size of the left child of node v =
 // Hex[(2v+1) << (L-l-1)] - Hex[2v << (L-l-1)]; ZB_l = exclusive scan of Z_l;
 // OB_l[v] = Hex[v << (L-l)] - ZB_l[v]; ZE_l[v] = ZB_l[v] + Z_l[v].
 // Level l's tables start at offset 2^l - 1.
@@ -214,10 +392,20 @@ __global__ void __launch_bounds__(kScanThreads) node_tables_kernel(const uint64_
     }
 }
 
-cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, uint64_t *ze, cudaStream_t st) {
+cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, uint64_t *ze, cudaStream_t st,
+                               uint64_t *tmp) {
     if (L == 0) return cudaSuccess;
-    node_tables_kernel<<<L, kScanThreads, 0, st>>>(hex, L, ob, ze);
-    return cudaGetLastError();
+    // Levels with up to kSingleCtaMax nodes: one CTA each, one launch.
+    uint32_t small = 0;
+    while (small < L && (1ull << small) <= kSingleCtaMax) small++;
+    if (tmp == nullptr) small = L;
+    node_tables_kernel<<<small, kScanThreads, 0, st>>>(hex, L, ob, ze);
+    cudaError_t e = cudaGetLastError();
+    for (uint32_t l = small; l < L && e == cudaSuccess; l++) {
+        const uint64_t nodes = 1ull << l;
+        e = scan_large(ZeroVal{hex, L - l}, TableOut{hex, L - l, ob + (nodes - 1), ze + (nodes - 1)}, nodes, tmp, st);
+    }
+    return e;
 }
 
 }  // namespace wt

@@ -567,14 +567,24 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
                 const uint32_t q = wbase + 128u * k + 4u * lane;
                 const uint32_t ob = crun + ((lpk[k >> 2] >> (8 * (k & 3))) & 0xffu);  // ones before q in the tile
                 crun += (tpk[k >> 2] >> (8 * (k & 3))) & 0xffu;
-                const uint32_t po = Zt + ob, pz = q - ob;
+                uint32_t po = Zt + ob, pz = q - ob;  // next slot of a one / of a zero
                 const uint32_t *e = &ew[k * kW];
+                if (full_tile) {
 #pragma unroll
-                for (int x = 0; x < 4; x++) {
-                    const uint32_t below = __popc(nb & ((1u << x) - 1u));  // ones among the lane's earlier symbols
-                    const uint32_t bit = (nb >> x) & 1u;
-                    const uint32_t dst = bit ? po + below : pz + x - below;
-                    if (full_tile || q + x < cnt) split[dst] = (Sym)step_sym<Sym>(e, x);
+                    for (int x = 0; x < 4; x++) {
+                        const bool bit = (nb >> x) & 1u;
+                        split[bit ? po : pz] = (Sym)step_sym<Sym>(e, x);
+                        po += bit;
+                        pz += !bit;
+                    }
+                } else {
+#pragma unroll
+                    for (int x = 0; x < 4; x++) {
+                        const bool bit = (nb >> x) & 1u;
+                        if (q + x < cnt) split[bit ? po : pz] = (Sym)step_sym<Sym>(e, x);
+                        po += bit;
+                        pz += !bit;
+                    }
                 }
             }
         }

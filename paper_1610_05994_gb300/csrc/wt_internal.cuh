@@ -266,6 +266,7 @@ struct BuildScratch {
     uint64_t *hex;        // 2^L + 1
     uint64_t *ob;         // 2^L - 1 : ones before each node's start
     uint64_t *ze;         // 2^L - 1 : zeros up to each node's end
+    uint64_t *scan_tmp;   // scan_tmp_bytes(L)
     uint64_t *status;     // L * ntiles look-back words
     uint32_t *tickets;    // L tile tickets
     void *ping;           // n * width
@@ -276,11 +277,21 @@ struct BuildScratch {
 // range check; then the exclusive scan into hex.
 cudaError_t launch_histogram(const void *S, uint64_t n, int width, uint64_t sigma, uint64_t *hist,
                              uint32_t *err, cudaStream_t st);
+// Large alphabets with n < 2^32: hist_replicas(n, sigma) replicas (0 = use
+// launch_histogram instead) of sigma u32 counters, zeroed by the caller.
+uint32_t hist_replicas(uint64_t n, uint64_t sigma);
+cudaError_t launch_histogram_replicated(const void *S, uint64_t n, int width, uint64_t sigma, uint32_t *rep,
+                                        uint32_t R, uint32_t *err, cudaStream_t st);
+cudaError_t launch_node_starts_replicated(const uint32_t *rep, uint32_t R, uint64_t sigma, uint32_t L,
+                                          uint64_t *hex, cudaStream_t st, uint64_t *tmp);
+// tmp (scan_tmp_bytes(L) bytes) lets large alphabets scan with many CTAs;
+// with tmp == nullptr one CTA scans everything.
 cudaError_t launch_node_starts(const uint64_t *hist, uint64_t sigma, uint32_t L, uint64_t n,
-                               uint64_t *hex, cudaStream_t st);
-// Per-level node tables ob/ze from hex.
+                               uint64_t *hex, cudaStream_t st, uint64_t *tmp = nullptr);
+// Per-level node tables ob/ze from hex (tmp as above).
 cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, uint64_t *ze,
-                               cudaStream_t st);
+                               cudaStream_t st, uint64_t *tmp = nullptr);
+size_t scan_tmp_bytes(uint32_t L);
 
 // Kernels (b)+(c): one level pass.  status/tickets must be zeroed.
 uint32_t lw_tile_elems(int width);
@@ -288,11 +299,23 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out,
                               uint64_t *status, uint32_t *ticket, uint32_t *err, cudaStream_t st);
 
-// Kernel (d): dd-direct build of all levels for small sigma.
-bool dd_supported(uint64_t sigma, int width);
-size_t dd_scratch_bytes(uint64_t n, uint64_t sigma, int width);
-cudaError_t launch_dd_build(const void *S, uint64_t n, int width, uint64_t sigma, uint32_t L,
-                            const uint64_t *hex, TreeDesc *d_desc, const TreeDesc &h_desc, void *scratch,
+// Kernel (d): dd-direct build of all levels for small sigma (dd.cu).
+struct DdScratch {
+    uint32_t *cnt;   // [tiles][sigma] per-tile leaf counts
+    uint32_t *off;   // [tiles][sigma] symbols of earlier tiles per leaf
+    uint32_t *csum;  // column-scan chunk sums
+    uint64_t *H;     // leaf histogram
+};
+bool dd_supported(uint64_t n, uint64_t sigma, int width);
+uint64_t dd_tiles(uint64_t n);
+size_t dd_scratch_bytes(uint64_t n, uint64_t sigma);
+DdScratch dd_carve(void *scratch, uint64_t n, uint64_t sigma);
+cudaError_t launch_dd_count(const void *S, uint64_t n, uint64_t sigma, const DdScratch &d, uint32_t *err,
+                            cudaStream_t st);
+cudaError_t launch_dd_scan(uint64_t n, uint64_t sigma, const DdScratch &d, cudaStream_t st);
+// The caller zeroes every level's bitmap words first (runs are OR-ed in).
+cudaError_t launch_dd_write(const void *S, uint64_t n, uint64_t sigma, uint32_t L, const TreeDesc &h_desc,
+                            TreeDesc *d_desc, const DdScratch &d, const uint64_t *hex, const uint64_t *ob,
                             uint32_t *err, cudaStream_t st);
 
 // Kernel (e): queries.

@@ -13,23 +13,46 @@ pytestmark = [pytest.mark.gpu, needs_gpu]
 WORKLOAD_SMALL = inputs.WORKLOADS["u8-uniform-2^20-s256"]
 
 
-def test_small_workload_bit_exact():
+VARIANTS = [1, 2]  # level-wise (kernels a+b+c), dd-direct (kernel d)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_small_workload_bit_exact(variant):
     """2^20 uniform bytes over 256 codes (8 levels): the full tree equals the oracle's."""
     W = wt()
     S = WORKLOAD_SMALL.generate()
-    t = W.Tree.build(to_dev(S), WORKLOAD_SMALL.sigma)
+    t = W.Tree.build(to_dev(S), WORKLOAD_SMALL.sigma, variant=variant)
+    assert t.info()["variant"] == variant
     compare_tree(t, S, WORKLOAD_SMALL.sigma)
 
 
-SIZES = [0, 1, 31, 32, 33, 511, 512, 513, 4095, 4096, 4097, 8193, 65535, 65537, 100003]
+def test_auto_variant_is_one_of_the_two_and_levelwise_for_wide_symbols():
+    W = wt()
+    a = W.Tree.build(to_dev(inputs.uniform(5000, 96, 1, np.uint8)), 96)
+    b = W.Tree.build(to_dev(inputs.uniform(5000, 1000, 1, np.uint16)), 1000)
+    assert a.info()["variant"] in (W.VARIANT_DD, W.VARIANT_LEVELWISE)
+    assert b.info()["variant"] == W.VARIANT_LEVELWISE
 
 
-@pytest.mark.parametrize("sigma", [1, 2, 3, 4, 5, 16, 17, 96, 256])
+def test_dd_rejects_what_it_cannot_build():
+    W = wt()
+    with pytest.raises(W.WTError) as e:
+        W.Tree.build(to_dev(inputs.uniform(100, 1000, 1, np.uint16)), 1000, variant=W.VARIANT_DD)
+    assert e.value.status == W.ERR_ARG
+
+
+SIZES = [0, 1, 31, 32, 33, 511, 512, 513, 4095, 4096, 4097, 8193, 16383, 16384, 16385, 65535, 65537, 100003]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("sigma", [1, 2, 3, 4, 5, 16, 17, 96, 255, 256])
 @pytest.mark.parametrize("n", SIZES)
-def test_edge_shapes_u8(sigma, n):
+def test_edge_shapes_u8(sigma, n, variant):
     W = wt()
     S = inputs.zipf(n, sigma, 1.0, 1000 + n, np.uint8) if n else np.zeros(0, np.uint8)
-    t = W.Tree.build(to_dev(S), sigma)
+    if variant == W.VARIANT_DD and (sigma == 1 or n == 0):
+        variant = W.VARIANT_AUTO  # nothing for dd to build
+    t = W.Tree.build(to_dev(S), sigma, variant=variant)
     compare_tree(t, S, sigma)
 
 
@@ -123,13 +146,14 @@ def test_async_build_on_stream_and_torch_allocator():
         W.use_torch_allocator(False)
 
 
-@pytest.mark.parametrize("sigma,dtype,log2n,alpha", [(96, np.uint8, 25, 1.0), (4, np.uint8, 25, 0.0),
-                                                     (65536, np.uint16, 23, 1.1), (1 << 20, np.uint32, 22, 1.2)])
-def test_many_tiles_per_cta_pipeline(sigma, dtype, log2n, alpha):
+@pytest.mark.parametrize("sigma,dtype,log2n,alpha,variant", [
+    (96, np.uint8, 25, 1.0, 1), (4, np.uint8, 25, 0.0, 1), (96, np.uint8, 25, 1.0, 2), (4, np.uint8, 25, 0.0, 2),
+    (256, np.uint8, 24, 0.0, 2), (65536, np.uint16, 23, 1.1, 1), (1 << 20, np.uint32, 22, 1.2, 1)])
+def test_many_tiles_per_cta_pipeline(sigma, dtype, log2n, alpha, variant):
     """Enough tiles that every persistent CTA streams several (the producer /
     compute pipeline runs at full depth), plus a ragged tail."""
     W = wt()
     n = (1 << log2n) + 777
     S = inputs.zipf(n, sigma, alpha, 4242, dtype) if alpha else inputs.uniform(n, sigma, 4242, dtype)
-    t = W.Tree.build(to_dev(S), sigma)
+    t = W.Tree.build(to_dev(S), sigma, variant=variant)
     compare_tree(t, S, sigma)
