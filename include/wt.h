@@ -98,11 +98,17 @@ wt_handle wt_build_async(const void *S, uint64_t n, uint64_t sigma, int sym_widt
 wt_status wt_wait(wt_handle h);
 
 /*
- * Builds count trees in one batched, graph-launched pass (the sequences may
- * differ in n, sigma and width).  S[k] are device pointers.  out[k] receives
- * each handle (NULL on argument errors, then the call returns the first
- * error).  Asynchronous on stream; wt_wait on any handle returns the batch's
- * status.
+ * Builds count trees in one batch (the sequences may differ in n, sigma and
+ * width): one launch computes every sequence's histogram, one its node
+ * starts, one its node tables, then one launch per (symbol width, level)
+ * runs the level pass of Algorithm 1's levels over every sequence that has
+ * that level.  On a non-default stream the launches are captured into one
+ * CUDA graph and launched together.  The trees share one device block,
+ * released when the last of them is freed.  S[k] are device pointers
+ * (n[k] < 2^40).  Any argument error builds nothing: every out[k] is NULL
+ * and the error is returned.  Asynchronous on stream; wt_wait on a handle
+ * returns that sequence's status (a device-side give-up anywhere in the
+ * batch is reported by every handle).
  */
 wt_status wt_build_batch(const void *const *S, const uint64_t *n, const uint64_t *sigma,
                          const int *sym_width, uint32_t count, wt_handle *out, void *stream);

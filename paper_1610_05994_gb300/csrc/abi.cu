@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -102,19 +104,24 @@ Profiler g_prof;
 struct ProfScope {
     int idx = -1;
     cudaStream_t st;
+    unsigned flags = cudaEventRecordDefault;
     ProfScope(int kid, double bytes, cudaStream_t s) : st(s) {
         std::lock_guard<std::mutex> lk(g_prof.mu);
         if (!g_prof.on) return;
         ProfRecord r{kid, bytes, g_prof.take(), g_prof.take()};
         if (!r.e0 || !r.e1) return;
-        cudaEventRecord(r.e0, st);
+        // Inside a stream capture the records become event nodes of the graph.
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cudaGetLastError();
+        if (cap == cudaStreamCaptureStatusActive) flags = cudaEventRecordExternal;
+        cudaEventRecordWithFlags(r.e0, st, flags);
         idx = (int)g_prof.recs.size();
         g_prof.recs.push_back(r);
     }
     ~ProfScope() {
         if (idx < 0) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
-        cudaEventRecord(g_prof.recs[idx].e1, st);
+        cudaEventRecordWithFlags(g_prof.recs[idx].e1, st, flags);
     }
 };
 
@@ -157,7 +164,26 @@ Shape shape_of(uint64_t n) {
 
 }  // namespace
 
+// Device memory shared by the trees of one wt_build_batch call: the block
+// is released when the last of its trees is freed.
+struct BatchShared {
+    Allocator alloc{};
+    void *mem = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    uint32_t *d_err = nullptr;  // the batch's level passes (timeouts)
+    std::mutex mu;
+    bool err_read = false;
+    uint32_t h_err = 0;
+    ~BatchShared() {
+        if (done) cudaEventDestroy(done);
+        if (mem) dev_free(alloc, mem, bytes, stream);
+    }
+};
+
 struct wt_tree {
+    std::shared_ptr<BatchShared> batch;  // set for trees built by wt_build_batch
     uint64_t n = 0, sigma = 0;
     uint32_t L = 0;
     int width = 0;
@@ -239,8 +265,9 @@ wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t si
     const size_t zeroed = hist + status + tickets;
     const size_t buf = align256(n * (uint64_t)width);
     const size_t stmp = align256(scan_tmp_bytes(L));
+    const size_t jslot = level_job_slot_bytes();
     const int nbuf = need_levels ? (L >= 3 ? 2 : (L == 2 ? 1 : 0)) : 0;
-    sc.bytes = zeroed + hex + 2 * tab + stmp + nbuf * buf;
+    sc.bytes = zeroed + hex + 2 * tab + stmp + jslot + nbuf * buf;
     sc.mem = dev_alloc(A, sc.bytes, st);
     if (!sc.mem) return WT_ERR_OOM;
     char *p = static_cast<char *>(sc.mem);
@@ -258,6 +285,8 @@ wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t si
     p += tab;
     sc.b.scan_tmp = reinterpret_cast<uint64_t *>(p);
     p += stmp;
+    sc.b.job_slot = p;
+    p += jslot;
     sc.b.ping = nbuf >= 1 ? p : nullptr;
     p += nbuf >= 1 ? buf : 0;
     sc.b.pong = nbuf >= 2 ? p : nullptr;
@@ -305,7 +334,8 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
             const double bytes = nw + t->n / 8.0 + t->n / 128.0 + (nxt ? nw : 0.0);
             ProfScope p(K_LEVEL_PASS, bytes, st);
             WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
-                                    &t->d_desc->lv[l].ones, b.status + l * ntiles, b.tickets + l, t->d_err, st));
+                                    &t->d_desc->lv[l].ones, b.status + l * ntiles, b.tickets + l, t->d_err, b.job_slot,
+                                    st));
             cur = nxt;
         }
     }
@@ -398,9 +428,20 @@ wt_status enqueue_build(wt_tree *t, const void *S, int variant, cudaStream_t st)
 wt_status finalize(wt_tree *t) {
     if (t->finalized) return t->status;
     t->finalized = true;
-    if (cudaEventSynchronize(t->done) != cudaSuccess) {
+    if (cudaEventSynchronize(t->batch ? t->batch->done : t->done) != cudaSuccess) {
         cudaGetLastError();
         return t->status = WT_ERR_CUDA;
+    }
+    if (t->batch) {
+        std::lock_guard<std::mutex> lk(t->batch->mu);
+        if (!t->batch->err_read) {
+            if (cudaMemcpy(&t->batch->h_err, t->batch->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cudaGetLastError();
+                return t->status = WT_ERR_CUDA;
+            }
+            t->batch->err_read = true;
+        }
+        if (t->batch->h_err & kErrTimeout) t->status = WT_ERR_TIMEOUT;
     }
     uint32_t err = 0;
     TreeDesc d;
@@ -423,7 +464,328 @@ void tree_destroy(wt_tree *t) {
     if (!t) return;
     if (t->done) cudaEventDestroy(t->done);
     if (t->mem) dev_free(t->alloc, t->mem, t->mem_bytes, t->stream);
+    t->batch.reset();  // the batch block goes with its last tree
     delete t;
+}
+
+// ------------------------------------------------------------- batches
+
+// Pinned host staging for a batch's tables, reused across calls once the
+// copies of the previous call have completed.
+struct PinnedStaging {
+    std::mutex mu;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ready = nullptr;  // the last copies out of the buffer
+};
+PinnedStaging g_pinned;
+
+size_t level_bytes_of(uint64_t n) {
+    const Shape s = shape_of(n);
+    return s.words + s.R + s.Hy + 2 * s.S;
+}
+
+// Fills a tree descriptor's level pointers from a block of level arrays.
+void carve_levels(TreeDesc &d, char *p, uint64_t n, uint32_t L) {
+    const Shape s = shape_of(n);
+    for (uint32_t l = 0; l < L; l++) {
+        LevelDesc &v = d.lv[l];
+        v.words = reinterpret_cast<uint32_t *>(p);
+        p += s.words;
+        v.R = reinterpret_cast<uint32_t *>(p);
+        p += s.R;
+        v.Hy = reinterpret_cast<uint64_t *>(p);
+        p += s.Hy;
+        v.S1 = reinterpret_cast<uint32_t *>(p);
+        p += s.S;
+        v.S0 = reinterpret_cast<uint32_t *>(p);
+        p += s.S;
+        v.ones = 0;
+    }
+}
+
+// A batch: the trees share one device block; one launch per stage builds
+// the histograms, node starts and node tables of all sequences, then one
+// launch per (symbol width, level) runs the level pass over every sequence
+// that has that level.  The whole sequence of launches is captured into a
+// CUDA graph and launched once (unless the stream is already capturing).
+wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64_t *sigma, const int *width,
+                           uint32_t count, wt_handle *out, cudaStream_t st) {
+    for (uint32_t k = 0; k < count; k++) out[k] = nullptr;
+    for (uint32_t k = 0; k < count; k++) {
+        wt_status r = check_args(S[k], n[k], sigma[k], width[k]);
+        if (r != WT_OK) return r;
+        if (n[k] > 0 && !is_device_pointer(S[k])) return WT_ERR_ARG;
+        if (n[k] >= (1ull << 40)) return WT_ERR_ARG;
+    }
+    if (count == 0) return WT_OK;
+    const Allocator A = current_allocator();
+    auto B = std::make_shared<BatchShared>();
+    B->alloc = A;
+    B->stream = st;
+    if (cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return WT_ERR_CUDA;
+    }
+
+    // ---- tree block: batch error word, descriptors, error words, levels
+    std::vector<uint32_t> L(count);
+    const size_t desc_bytes = align256(sizeof(TreeDesc) * count);
+    const size_t errw_bytes = align256(4 * (size_t)count);
+    size_t tree_bytes = 256 + desc_bytes + errw_bytes;
+    std::vector<size_t> lvl_off(count);
+    for (uint32_t k = 0; k < count; k++) {
+        L[k] = levels_of(sigma[k]);
+        lvl_off[k] = tree_bytes;
+        tree_bytes += level_bytes_of(n[k]) * L[k];
+    }
+    B->bytes = tree_bytes;
+    B->mem = dev_alloc(A, tree_bytes, st);
+    if (!B->mem) return WT_ERR_OOM;
+    char *tb = static_cast<char *>(B->mem);
+    B->d_err = reinterpret_cast<uint32_t *>(tb);
+    TreeDesc *d_descs = reinterpret_cast<TreeDesc *>(tb + 256);
+    uint32_t *d_errs = reinterpret_cast<uint32_t *>(tb + 256 + desc_bytes);
+
+    std::vector<TreeDesc> hdesc(count);
+    std::vector<wt_tree *> trees(count, nullptr);
+    for (uint32_t k = 0; k < count; k++) {
+        TreeDesc &d = hdesc[k];
+        memset(&d, 0, sizeof(TreeDesc));
+        d.n = n[k];
+        d.sigma = sigma[k];
+        d.nblocks = ceil_div(n[k], kBlockBits);
+        d.L = L[k];
+        d.width = (uint32_t)width[k];
+        carve_levels(d, tb + lvl_off[k], n[k], L[k]);
+    }
+
+    // ---- scratch: per sequence histogram, node starts, node tables,
+    // look-back words, ping-pong orders; then the batch tables.
+    struct Off {
+        size_t hist, hex, ob, ze, status, ping, pong;
+    };
+    std::vector<Off> so(count);
+    size_t zeroed = 256;  // tickets live in the first 256 bytes
+    for (uint32_t k = 0; k < count; k++) {
+        so[k].hist = zeroed;
+        zeroed += align256(sigma[k] * 8);
+        so[k].status = zeroed;
+        zeroed += align256((size_t)L[k] * ceil_div(n[k], lw_tile_elems(width[k])) * 8);
+    }
+    size_t sbytes = zeroed;
+    for (uint32_t k = 0; k < count; k++) {
+        const size_t leaves = L[k] ? (1ull << L[k]) : 0;
+        so[k].hex = sbytes;
+        sbytes += align256((leaves + 1) * 8);
+        so[k].ob = sbytes;
+        sbytes += align256(leaves * 8);
+        so[k].ze = sbytes;
+        sbytes += align256(leaves * 8);
+        const size_t buf = align256(n[k] * (uint64_t)width[k]);
+        so[k].ping = sbytes;
+        sbytes += L[k] >= 2 ? buf : 0;
+        so[k].pong = sbytes;
+        sbytes += L[k] >= 3 ? buf : 0;
+    }
+    // Level jobs per (width class, level).
+    uint32_t maxL[3] = {0, 0, 0};
+    auto wclass = [](int w) { return w == 1 ? 0 : (w == 2 ? 1 : 2); };
+    for (uint32_t k = 0; k < count; k++) maxL[wclass(width[k])] = std::max(maxL[wclass(width[k])], L[k]);
+    struct LaunchPlan {
+        int width;
+        uint32_t l;
+        std::vector<uint32_t> seqs;
+        size_t jobs_off, ts_off;  // in the staging tables
+        uint32_t total;
+    };
+    std::vector<LaunchPlan> plans;
+    for (int c = 0; c < 3; c++)
+        for (uint32_t l = 0; l < maxL[c]; l++) {
+            LaunchPlan P;
+            P.width = c == 0 ? 1 : (c == 1 ? 2 : 4);
+            P.l = l;
+            for (uint32_t k = 0; k < count; k++)
+                if (wclass(width[k]) == c && L[k] > l && n[k] > 0) P.seqs.push_back(k);
+            if (!P.seqs.empty()) plans.push_back(std::move(P));
+        }
+    if (plans.size() > 64) return WT_ERR_ARG;  // ticket area holds 64 launches
+
+    // Staging layout (same offsets on host and device).
+    size_t tbytes = 0;
+    const size_t seqjob_off = tbytes;
+    tbytes += align256(sizeof(SeqJob) * count);
+    const size_t hts_off = tbytes;
+    tbytes += align256(4 * ((size_t)count + 1));
+    const size_t lts_off = tbytes;
+    tbytes += align256(4 * ((size_t)count + 1));
+    for (auto &P : plans) {
+        P.jobs_off = tbytes;
+        tbytes += align256(sizeof(LevelJob) * P.seqs.size());
+        P.ts_off = tbytes;
+        tbytes += align256(4 * (P.seqs.size() + 1));
+    }
+    const size_t total_scratch = sbytes + tbytes;
+    void *scratch = dev_alloc(A, total_scratch, st);
+    if (!scratch) return WT_ERR_OOM;
+    char *sc = static_cast<char *>(scratch);
+    char *dt = sc + sbytes;  // device tables
+
+    // Host tables, staged in pinned memory.
+    std::lock_guard<std::mutex> lk(g_pinned.mu);
+    const size_t stage_bytes = tbytes + desc_bytes;
+    if (g_pinned.ready && cudaEventSynchronize(g_pinned.ready) != cudaSuccess) cudaGetLastError();
+    if (g_pinned.bytes < stage_bytes) {
+        if (g_pinned.ptr) cudaFreeHost(g_pinned.ptr);
+        g_pinned.ptr = nullptr;
+        g_pinned.bytes = 0;
+        if (cudaMallocHost(&g_pinned.ptr, stage_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            dev_free(A, scratch, total_scratch, st);
+            return WT_ERR_OOM;
+        }
+        g_pinned.bytes = stage_bytes;
+    }
+    if (!g_pinned.ready && cudaEventCreateWithFlags(&g_pinned.ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free(A, scratch, total_scratch, st);
+        return WT_ERR_CUDA;
+    }
+    char *ht = static_cast<char *>(g_pinned.ptr);
+    SeqJob *hjobs = reinterpret_cast<SeqJob *>(ht + seqjob_off);
+    uint32_t *hts = reinterpret_cast<uint32_t *>(ht + hts_off);
+    uint32_t *lts = reinterpret_cast<uint32_t *>(ht + lts_off);
+    uint32_t hist_tiles = 0, total_levels = 0;
+    for (uint32_t k = 0; k < count; k++) {
+        SeqJob &J = hjobs[k];
+        J.S = S[k];
+        J.n = n[k];
+        J.sigma = sigma[k];
+        J.L = L[k];
+        J.width = (uint32_t)width[k];
+        J.hist = reinterpret_cast<uint64_t *>(sc + so[k].hist);
+        J.hex = reinterpret_cast<uint64_t *>(sc + so[k].hex);
+        J.ob = reinterpret_cast<uint64_t *>(sc + so[k].ob);
+        J.ze = reinterpret_cast<uint64_t *>(sc + so[k].ze);
+        J.err = d_errs + k;
+        hts[k] = hist_tiles;
+        hist_tiles += batch_hist_tiles(n[k]);
+        lts[k] = total_levels;
+        total_levels += L[k];
+    }
+    hts[count] = hist_tiles;
+    lts[count] = total_levels;
+    for (auto &P : plans) {
+        LevelJob *pj = reinterpret_cast<LevelJob *>(ht + P.jobs_off);
+        uint32_t *pts = reinterpret_cast<uint32_t *>(ht + P.ts_off);
+        uint32_t tiles = 0;
+        for (size_t q = 0; q < P.seqs.size(); q++) {
+            const uint32_t k = P.seqs[q];
+            const uint32_t l = P.l;
+            const uint64_t ntk = ceil_div(n[k], lw_tile_elems(width[k]));
+            const void *cur = l == 0 ? S[k] : sc + ((l & 1) ? so[k].ping : so[k].pong);
+            void *nxt = sc + ((l & 1) ? so[k].pong : so[k].ping);
+            pj[q] = make_level_job(cur, nxt, n[k], width[k], L[k], l, reinterpret_cast<uint64_t *>(sc + so[k].ob),
+                                   reinterpret_cast<uint64_t *>(sc + so[k].ze), hdesc[k].lv[l],
+                                   &d_descs[k].lv[l].ones, reinterpret_cast<uint64_t *>(sc + so[k].status) + l * ntk);
+            pts[q] = tiles;
+            tiles += (uint32_t)ntk;
+        }
+        pts[P.seqs.size()] = tiles;
+        P.total = tiles;
+    }
+    memcpy(ht + tbytes, hdesc.data(), sizeof(TreeDesc) * count);
+
+    // ---- device work (captured into one graph when the stream is idle-capturable)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    const bool use_graph = cap == cudaStreamCaptureStatusNone && st != nullptr;
+    cudaGraph_t graph = nullptr;
+    wt_status r = WT_OK;
+    if (use_graph && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && r == WT_OK) r = WT_ERR_CUDA;
+    };
+    if (r == WT_OK) {
+        ck(cudaMemsetAsync(sc, 0, zeroed, st));
+        ck(cudaMemsetAsync(B->d_err, 0, 4, st));
+        ck(cudaMemcpyAsync(dt, ht, tbytes, cudaMemcpyHostToDevice, st));
+        ck(cudaMemcpyAsync(d_descs, ht + tbytes, sizeof(TreeDesc) * count, cudaMemcpyHostToDevice, st));
+        // empty sequences: R[0] = Hy[0] = 0
+        for (uint32_t k = 0; k < count; k++)
+            if (n[k] == 0)
+                for (uint32_t l = 0; l < L[k]; l++) {
+                    ck(cudaMemsetAsync(hdesc[k].lv[l].R, 0, 4, st));
+                    ck(cudaMemsetAsync(hdesc[k].lv[l].Hy, 0, 8, st));
+                }
+        {
+            double nw = 0;
+            for (uint32_t k = 0; k < count; k++) nw += (double)n[k] * width[k];
+            ProfScope p(K_HIST, nw, st);
+            ck(launch_batch_prepare(reinterpret_cast<const SeqJob *>(dt + seqjob_off), count,
+                                    reinterpret_cast<const uint32_t *>(dt + hts_off), hist_tiles,
+                                    reinterpret_cast<const uint32_t *>(dt + lts_off), total_levels, st));
+        }
+        uint32_t *tickets = reinterpret_cast<uint32_t *>(sc);
+        for (size_t q = 0; q < plans.size(); q++) {
+            const LaunchPlan &P = plans[q];
+            double bytes = 0;
+            for (uint32_t k : P.seqs) {
+                const double nw = (double)n[k] * width[k];
+                bytes += nw + n[k] / 8.0 + n[k] / 128.0 + (P.l + 1 < L[k] ? nw : 0.0);
+            }
+            ProfScope p(K_LEVEL_PASS, bytes, st);
+            ck(launch_level_jobs(P.width, P.l, reinterpret_cast<const LevelJob *>(dt + P.jobs_off),
+                                 reinterpret_cast<const uint32_t *>(dt + P.ts_off), (uint32_t)P.seqs.size(), P.total,
+                                 tickets + q, B->d_err, st));
+        }
+    }
+    if (use_graph) {
+        if (cudaStreamEndCapture(st, &graph) != cudaSuccess) {
+            cudaGetLastError();
+            r = WT_ERR_CUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        if (r == WT_OK && (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess || cudaGraphLaunch(exec, st) != cudaSuccess)) {
+            cudaGetLastError();
+            r = WT_ERR_CUDA;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    ck(cudaEventRecord(g_pinned.ready, st));
+    ck(cudaEventRecord(B->done, st));
+    dev_free(A, scratch, total_scratch, st);  // stream-ordered, after the batch
+    if (r != WT_OK) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        return r;
+    }
+    for (uint32_t k = 0; k < count; k++) {
+        wt_tree *t = new (std::nothrow) wt_tree();
+        if (!t) {
+            for (uint32_t q = 0; q < k; q++) tree_destroy(trees[q]);
+            return WT_ERR_OOM;
+        }
+        t->batch = B;
+        t->n = n[k];
+        t->sigma = sigma[k];
+        t->L = L[k];
+        t->width = width[k];
+        t->variant = WT_VARIANT_LEVELWISE;
+        t->alloc = A;
+        t->stream = st;
+        t->d_desc = d_descs + k;
+        t->d_err = d_errs + k;
+        t->h_desc = hdesc[k];
+        t->mem_bytes = level_bytes_of(n[k]) * L[k] + sizeof(TreeDesc) + 4;
+        trees[k] = t;
+    }
+    for (uint32_t k = 0; k < count; k++) out[k] = trees[k];
+    return WT_OK;
 }
 
 wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int variant, cudaStream_t st) {
@@ -522,13 +884,7 @@ wt_status wt_wait(wt_handle h) {
 wt_status wt_build_batch(const void *const *S, const uint64_t *n, const uint64_t *sigma, const int *sym_width,
                          uint32_t count, wt_handle *out, void *stream) {
     if (count > 0 && (!S || !n || !sigma || !sym_width || !out)) return set_last(WT_ERR_ARG);
-    wt_status first = WT_OK;
-    for (uint32_t k = 0; k < count; k++) {
-        out[k] = build_async(S[k], n[k], sigma[k], sym_width[k], WT_VARIANT_AUTO,
-                             static_cast<cudaStream_t>(stream));
-        if (!out[k] && first == WT_OK) first = g_last;
-    }
-    return set_last(first);
+    return set_last(build_batch_impl(S, n, sigma, sym_width, count, out, static_cast<cudaStream_t>(stream)));
 }
 
 wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, void *stream) {
@@ -736,7 +1092,7 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
     const size_t tab = align256((1ull << L) * 8);
     const size_t status = align256(ntiles * 8);
     const size_t zeroed = status + 256;
-    const size_t bytes = zeroed + 2 * tab + s.Hy + 2 * s.S + 256;
+    const size_t bytes = zeroed + 2 * tab + s.Hy + 2 * s.S + 256 + level_job_slot_bytes();
     void *mem = dev_alloc(A, bytes, st);
     if (!mem) return set_last(WT_ERR_OOM);
     char *p = static_cast<char *>(mem);
@@ -759,12 +1115,14 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
     lv.S0 = reinterpret_cast<uint32_t *>(p);
     p += s.S;
     uint64_t *ones = reinterpret_cast<uint64_t *>(p);
+    p += 256;
+    void *job_slot = p;
     lv.ones = 0;
     uint32_t herr = 0;
     if (cudaMemsetAsync(mem, 0, zeroed, st) != cudaSuccess ||
         launch_node_tables(Hex, L, ob, ze, st) != cudaSuccess ||
         launch_level_pass(cur, (l + 1 < L) ? nxt : nullptr, n, sym_width, L, l, ob, ze, lv, ones, stw, ticket, err,
-                          st) != cudaSuccess ||
+                          job_slot, st) != cudaSuccess ||
         cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
         cudaGetLastError();
         r = WT_ERR_CUDA;

@@ -53,26 +53,31 @@ struct LwCfg {
 
 uint32_t lw_tile_elems(int width) { return kLwTileBytes / (uint32_t)width; }
 
-struct LevelArgs {
-    const void *cur;
-    void *nxt;            // nullptr on the last level
-    uint64_t n;
-    uint64_t nblocks;
-    uint64_t nspans;
-    uint32_t L, l;
-    uint32_t ntiles;
-    LevelDesc lv;
-    uint64_t *ones_out;
-    const uint64_t *ob;   // level l's table (already offset)
-    const uint64_t *ze;
-    uint64_t *status;     // ntiles look-back words of this level
+struct LevelLaunch {
+    const LevelJob *jobs;        // device array of njobs
+    const uint32_t *tile_start;  // device, njobs + 1: first global tile of each job
+    uint32_t njobs, total_tiles, l;
     uint32_t *ticket;
     uint32_t *err;
 };
 
+// Job of global tile t: the largest k with tile_start[k] <= t.
+__device__ __forceinline__ uint32_t find_job(const LevelLaunch &a, uint32_t t) {
+    uint32_t lo = 0, hi = a.njobs - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (a.tile_start[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // Per split-slot record of a tile waiting for its placement.
 struct TileMeta {
-    uint32_t tile, cnt, ones;
+    LevelJob J;                          // the tile's sequence
+    uint32_t tile, cnt, ones;            // tile index inside the sequence
     uint32_t wexcl[kCompWarps];          // ones before each warp's range
     uint32_t cpre[kCompWarps][8];        // ones before each step inside the warp's range
 };
@@ -80,6 +85,7 @@ struct TileMeta {
 struct LwShared {
     uint64_t full[2], empty[2], pre[2];
     uint64_t prefix[4];    // ones before tile index i of this CTA, at [i & 3]
+    LevelJob job[2];       // sequence of the tile in each input slot
     uint32_t in_tile[2];
     uint32_t wtot[kCompWarps];
     uint32_t abort;
@@ -207,8 +213,9 @@ __device__ __forceinline__ void realign16(const uint32_t (&prev)[4], const uint3
 // Places tile `m` from its split slot: the directory entries that need the
 // global prefix, then every symbol to P_{l+1}.  Run by the compute warps.
 template <typename Sym>
-__device__ void place_tile(const LevelArgs &a, const TileMeta &m, uint64_t prefix, const Sym *__restrict__ split,
-                           int ct, bool &bad) {
+__device__ void place_tile(const TileMeta &m, uint32_t l, uint64_t prefix, const Sym *__restrict__ split, int ct,
+                           bool &bad) {
+    const LevelJob &a = m.J;
     using Cfg = LwCfg<Sym>;
     constexpr uint32_t kPerLane = 16 / sizeof(Sym);     // symbols per lane per chunk
     constexpr uint32_t kChunk = 32 * kPerLane;          // symbols per warp chunk (512 bytes)
@@ -262,8 +269,8 @@ __device__ void place_tile(const LevelArgs &a, const TileMeta &m, uint64_t prefi
     // store whole vectors; only the two ragged ends use narrower stores.
     Sym *nxt = static_cast<Sym *>(a.nxt);
     const uint64_t zeros_prefix = base - prefix;  // zeros before this tile
-    const uint32_t shv = a.L - a.l;               // key_l = s >> (L - l)
-    const uint32_t nodes = 1u << a.l;
+    const uint32_t shv = a.L - l;                 // key_l = s >> (L - l)
+    const uint32_t nodes = 1u << l;
     for (uint32_t q0 = warp * kChunk; q0 < cnt; q0 += kCompWarps * kChunk) {
         const uint32_t q = q0 + kPerLane * lane;
         const uint4 xv = *reinterpret_cast<const uint4 *>(&split[q]);
@@ -319,8 +326,18 @@ __device__ void place_tile(const LevelArgs &a, const TileMeta &m, uint64_t prefi
     }
 }
 
+// Bytes of tile `tile` of job J that a 16-byte-granular bulk copy can bring
+// in (0 when the job's symbols are not 16-byte aligned: then every symbol is
+// read from global memory directly).
 template <typename Sym>
-__global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) {
+__device__ __forceinline__ uint32_t tile_bytes16(const LevelJob &J, uint32_t tile) {
+    if (reinterpret_cast<uintptr_t>(J.cur) & 15) return 0;
+    const uint64_t left = (J.n - (uint64_t)tile * LwCfg<Sym>::kTile) * sizeof(Sym);
+    return (uint32_t)(left < kLwTileBytes ? left : kLwTileBytes) & ~15u;
+}
+
+template <typename Sym>
+__global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelLaunch a) {
     using Cfg = LwCfg<Sym>;
     constexpr int kSteps = Cfg::kSteps;
     constexpr int kW = Cfg::kWordsPerStep;
@@ -330,15 +347,7 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
     LwShared &sh = *reinterpret_cast<LwShared *>(smem + 4 * kLwTileBytes);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const Sym *cur = static_cast<const Sym *>(a.cur);
-    const bool tma = (reinterpret_cast<uintptr_t>(cur) & 15) == 0;
-    auto tile_bytes16 = [&](uint32_t tile) -> uint32_t {
-        if (!tma) return 0;
-        const uint64_t left = (a.n - (uint64_t)tile * Cfg::kTile) * sizeof(Sym);
-        return (uint32_t)(left < kLwTileBytes ? left : kLwTileBytes) & ~15u;
-    };
-
-    const uint32_t bsh = a.L - 1 - a.l;  // the level-l bit of a symbol
+    const uint32_t l = a.l;
     if (tid == 0) {
         for (int s = 0; s < 2; s++) {
             mbar_init(&sh.full[s], 1);
@@ -359,13 +368,18 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
         // back for the oldest tile and hands its prefix to the compute warps.
         auto claim = [&](int s) -> uint32_t {  // lane 0: claim a ticket for slot s and stream it in
             const uint32_t t = atomicAdd(a.ticket, 1u);  // claim order: look-back waits only on earlier tiles
-            if (t < a.ntiles) {
-                sh.in_tile[s] = t;
+            if (t < a.total_tiles) {
+                const uint32_t k = find_job(a, t);
+                const uint32_t tile = t - a.tile_start[k];
+                sh.job[s] = a.jobs[k];
+                sh.in_tile[s] = tile;
+                const LevelJob &J = sh.job[s];
                 fence_proxy_async_smem();
-                const uint32_t bytes = tile_bytes16(t);
+                const uint32_t bytes = tile_bytes16<Sym>(J, tile);
                 if (bytes)
                     bulk_load(in_buf + s * kLwTileBytes,
-                              reinterpret_cast<const unsigned char *>(cur) + (uint64_t)t * kLwTileBytes, bytes, &sh.full[s]);
+                              reinterpret_cast<const unsigned char *>(J.cur) + (uint64_t)tile * kLwTileBytes, bytes,
+                              &sh.full[s]);
                 else
                     mbar_arrive(&sh.full[s]);
                 return t;
@@ -374,11 +388,15 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
             mbar_arrive(&sh.full[s]);
             return kEnd;
         };
-        // Ones of tile t held in slot s (whole warp; tail symbols from global).
-        auto count = [&](uint32_t t, int s) -> uint32_t {
-            const uint64_t base = (uint64_t)t * Cfg::kTile;
-            const uint32_t cnt = (uint32_t)((a.n - base) < (uint64_t)Cfg::kTile ? (a.n - base) : (uint64_t)Cfg::kTile);
-            const uint32_t b16 = tile_bytes16(t);
+        // Ones of the tile held in slot s (whole warp; tail symbols from global).
+        auto count = [&](int s) -> uint32_t {
+            const LevelJob &J = sh.job[s];
+            const uint32_t tile = sh.in_tile[s];
+            const uint32_t bsh = J.L - 1 - l;
+            const Sym *cur = static_cast<const Sym *>(J.cur);
+            const uint64_t base = (uint64_t)tile * Cfg::kTile;
+            const uint32_t cnt = (uint32_t)((J.n - base) < (uint64_t)Cfg::kTile ? (J.n - base) : (uint64_t)Cfg::kTile);
+            const uint32_t b16 = tile_bytes16<Sym>(J, tile);
             const uint4 *v = reinterpret_cast<const uint4 *>(in_buf + s * kLwTileBytes);
             uint32_t c = 0;
             for (uint32_t k = lane; k < b16 / 16; k += 32) {
@@ -409,19 +427,19 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
         uint32_t agg = 0;
         if (t0 != kEnd) {
             ok = mbar_wait(&sh.full[0], 0);
-            agg = count(t0, 0);
-            if (lane == 0) publish_aggregate(a.status, t0, agg);
+            agg = count(0);
+            if (lane == 0) publish_aggregate(sh.job[0].status, sh.in_tile[0], agg);
         }
-        uint32_t tcur = t0, tnext = t1;
+        uint32_t tnext = t1;
         for (uint32_t i = 0; ok && i < issued; i++) {
             const int s = i & 1;
             uint32_t agg_next = 0;
             if (tnext != kEnd) {  // tile index i + 1, in the other slot
                 ok = mbar_wait(&sh.full[s ^ 1], ((i + 1) >> 1) & 1u);
-                agg_next = count(tnext, s ^ 1);
-                if (lane == 0) publish_aggregate(a.status, tnext, agg_next);
+                agg_next = count(s ^ 1);
+                if (lane == 0) publish_aggregate(sh.job[s ^ 1].status, sh.in_tile[s ^ 1], agg_next);
             }
-            const uint64_t prefix = lookback_published(a.status, tcur, agg, a.err);
+            const uint64_t prefix = lookback_published(sh.job[s].status, sh.in_tile[s], agg, a.err);
             // Hand the prefix over only once the compute warps have read tile
             // i: then they have also taken the previous prefix of this slot,
             // so pre[s] never runs two phases ahead of its waiters.
@@ -439,7 +457,6 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
                 else ended = true;
             }
             if (*(volatile uint32_t *)&sh.abort) ok = false;
-            tcur = tnext;
             tnext = tnn;
             agg = agg_next;
         }
@@ -464,11 +481,20 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
         // and record placed there are free from here on.
         if (bar_compute_any(failed || tile == kEnd || *(volatile uint32_t *)&sh.abort)) break;
         if (tid == 0) sh.consumed = i + 1;
-        const uint64_t base = (uint64_t)tile * Cfg::kTile;
-        const uint32_t cnt = (uint32_t)((a.n - base) < (uint64_t)Cfg::kTile ? (a.n - base) : (uint64_t)Cfg::kTile);
-        const uint32_t bytes16 = tile_bytes16(tile);
-        const unsigned char *src = in_buf + s * kLwTileBytes;
         TileMeta &m = sh.meta[s];
+        // The tile's sequence: everything this iteration needs is read before
+        // this warp releases the slot (the producer then refills it).
+        const LevelJob &Jin = sh.job[s];
+        const Sym *cur = static_cast<const Sym *>(Jin.cur);
+        const uint64_t jn = Jin.n, jnblocks = Jin.nblocks;
+        uint32_t *const jwords = Jin.lv.words;
+        const bool has_next = Jin.nxt != nullptr;
+        const uint32_t bsh = Jin.L - 1 - l;  // the level-l bit of a symbol
+        const uint64_t base = (uint64_t)tile * Cfg::kTile;
+        const uint32_t cnt = (uint32_t)((jn - base) < (uint64_t)Cfg::kTile ? (jn - base) : (uint64_t)Cfg::kTile);
+        const uint32_t bytes16 = tile_bytes16<Sym>(Jin, tile);
+        const unsigned char *src = in_buf + s * kLwTileBytes;
+        if (tid == 0) m.J = Jin;
 
         // Phase 1: read the lane's symbols, write the bitmap words, count.
         // A lane holds 4 consecutive symbols per 128-symbol step; the step's
@@ -522,7 +548,7 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
             nib |= nb << (4 * k);
             const uint32_t wv = __reduce_or_sync(gmask, nb << (4 * (lane & 7)));
             const uint64_t word = word0 + 4u * k;
-            if ((lane & 7) == 0 && word < a.nblocks * 16) a.lv.words[word] = wv;
+            if ((lane & 7) == 0 && word < jnblocks * 16) jwords[word] = wv;
             cpk[k >> 2] += (uint32_t)__popc(nb) << (8 * (k & 3));
         }
         // Exclusive per-lane prefixes (packed) and warp totals of every step.
@@ -558,7 +584,7 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
         // zeros to [0, Zt), ones to [Zt, cnt), order kept.  Each symbol's
         // slot follows from the ones before it: in the tile, in the warp's
         // step, in the lane.
-        if (a.nxt != nullptr) {
+        if (has_next) {
             Sym *split = split_buf + s * Cfg::kTile;
             uint32_t crun = warp_excl;
 #pragma unroll
@@ -593,7 +619,7 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
         if (i > 0) {
             const int ps = s ^ 1;
             if (mbar_wait(&sh.pre[ps], ((i - 1) >> 1) & 1u))
-                place_tile<Sym>(a, sh.meta[ps], sh.prefix[(i - 1) & 3], split_buf + ps * Cfg::kTile, tid, bad);
+                place_tile<Sym>(sh.meta[ps], l, sh.prefix[(i - 1) & 3], split_buf + ps * Cfg::kTile, tid, bad);
             else
                 failed = true;
         }
@@ -602,7 +628,7 @@ __global__ void __launch_bounds__(kLwThreads, 2) level_pass_kernel(LevelArgs a) 
     if (!bar_compute_any(failed || *(volatile uint32_t *)&sh.abort) && i > 0) {
         const int ps = (i - 1) & 1;
         if (mbar_wait(&sh.pre[ps], ((i - 1) >> 1) & 1u))
-            place_tile<Sym>(a, sh.meta[ps], sh.prefix[(i - 1) & 3], split_buf + ps * Cfg::kTile, tid, bad);
+            place_tile<Sym>(sh.meta[ps], l, sh.prefix[(i - 1) & 3], split_buf + ps * Cfg::kTile, tid, bad);
         else
             failed = true;
     }
@@ -631,7 +657,7 @@ static int lw_grid(const void *kernel, uint32_t ntiles) {
 }
 
 template <typename Sym>
-static cudaError_t launch_lw(const LevelArgs &a, cudaStream_t st) {
+static cudaError_t launch_lw(const LevelLaunch &a, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<Sym>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -639,29 +665,38 @@ static cudaError_t launch_lw(const LevelArgs &a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int grid = lw_grid((const void *)level_pass_kernel<Sym>, a.ntiles);
+    const int grid = lw_grid((const void *)level_pass_kernel<Sym>, a.total_tiles);
     level_pass_kernel<Sym><<<grid, kLwThreads, kLwSmem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
-                              const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out,
-                              uint64_t *status, uint32_t *ticket, uint32_t *err, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    LevelArgs a;
-    a.cur = cur;
-    a.nxt = (l + 1 < L) ? nxt : nullptr;
-    a.n = n;
-    a.nblocks = ceil_div(n, kBlockBits);
-    a.nspans = ceil_div(n, 1ull << kSpanShift);
-    a.L = L;
+LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l, const uint64_t *ob,
+                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint64_t *status) {
+    LevelJob j;
+    j.cur = cur;
+    j.nxt = (l + 1 < L) ? nxt : nullptr;
+    j.n = n;
+    j.nblocks = ceil_div(n, kBlockBits);
+    j.nspans = ceil_div(n, 1ull << kSpanShift);
+    j.L = L;
+    j.ntiles = (uint32_t)ceil_div(n, lw_tile_elems(width));
+    j.lv = lv;
+    j.ones_out = ones_out;
+    j.ob = ob + ((1ull << l) - 1);
+    j.ze = ze + ((1ull << l) - 1);
+    j.status = status;
+    return j;
+}
+
+cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
+                              uint32_t total_tiles, uint32_t *ticket, uint32_t *err, cudaStream_t st) {
+    if (njobs == 0 || total_tiles == 0) return cudaSuccess;
+    LevelLaunch a;
+    a.jobs = jobs;
+    a.tile_start = tile_start;
+    a.njobs = njobs;
+    a.total_tiles = total_tiles;
     a.l = l;
-    a.ntiles = (uint32_t)ceil_div(n, lw_tile_elems(width));
-    a.lv = lv;
-    a.ones_out = ones_out;
-    a.ob = ob + ((1ull << l) - 1);
-    a.ze = ze + ((1ull << l) - 1);
-    a.status = status;
     a.ticket = ticket;
     a.err = err;
     switch (width) {
@@ -670,6 +705,31 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
         case 4: return launch_lw<uint32_t>(a, st);
     }
     return cudaErrorInvalidValue;
+}
+
+// Writes one job and its tile range to device memory (kernel parameters
+// carry the values, so no host buffer has to outlive the call).
+__global__ void put_job_kernel(LevelJob j, LevelJob *dst, uint32_t *tile_start) {
+    *dst = j;
+    tile_start[0] = 0;
+    tile_start[1] = j.ntiles;
+}
+
+size_t level_job_bytes() { return sizeof(LevelJob); }
+
+size_t level_job_slot_bytes() { return (sizeof(LevelJob) + 2 * sizeof(uint32_t) + 255) & ~size_t(255); }
+
+cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
+                              const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out,
+                              uint64_t *status, uint32_t *ticket, uint32_t *err, void *job_slot, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, status);
+    LevelJob *dj = static_cast<LevelJob *>(job_slot);
+    uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
+    put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, ticket, err, st);
 }
 
 }  // namespace wt

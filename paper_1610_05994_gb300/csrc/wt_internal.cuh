@@ -267,6 +267,7 @@ struct BuildScratch {
     uint64_t *ob;         // 2^L - 1 : ones before each node's start
     uint64_t *ze;         // 2^L - 1 : zeros up to each node's end
     uint64_t *scan_tmp;   // scan_tmp_bytes(L)
+    void *job_slot;       // level_job_slot_bytes()
     uint64_t *status;     // L * ntiles look-back words
     uint32_t *tickets;    // L tile tickets
     void *ping;           // n * width
@@ -293,11 +294,32 @@ cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, ui
                                cudaStream_t st, uint64_t *tmp = nullptr);
 size_t scan_tmp_bytes(uint32_t L);
 
-// Kernels (b)+(c): one level pass.  status/tickets must be zeroed.
+// Kernels (b)+(c): one level pass (level.cu).  status/tickets must be
+// zeroed.  job_slot: level_job_slot_bytes() of device memory.
 uint32_t lw_tile_elems(int width);
+size_t level_job_slot_bytes();
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out,
-                              uint64_t *status, uint32_t *ticket, uint32_t *err, cudaStream_t st);
+                              uint64_t *status, uint32_t *ticket, uint32_t *err, void *job_slot, cudaStream_t st);
+// A batch: one launch runs level l of many sequences of one width (level.cu).
+// One sequence's share of a level launch (a batch launches many at once).
+struct LevelJob {
+    const void *cur;
+    void *nxt;                 // nullptr on the sequence's last level
+    uint64_t n, nblocks, nspans;
+    uint32_t L;                // the sequence's number of levels
+    uint32_t ntiles;           // its tiles at this width
+    LevelDesc lv;              // its level-l arrays
+    uint64_t *ones_out;
+    const uint64_t *ob, *ze;   // its level-l node tables
+    uint64_t *status;          // ntiles look-back words
+};
+
+LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l, const uint64_t *ob,
+                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint64_t *status);
+size_t level_job_bytes();
+cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
+                              uint32_t total_tiles, uint32_t *ticket, uint32_t *err, cudaStream_t st);
 
 // Kernel (d): dd-direct build of all levels for small sigma (dd.cu).
 struct DdScratch {
@@ -317,6 +339,21 @@ cudaError_t launch_dd_scan(uint64_t n, uint64_t sigma, const DdScratch &d, cudaS
 cudaError_t launch_dd_write(const void *S, uint64_t n, uint64_t sigma, uint32_t L, const TreeDesc &h_desc,
                             TreeDesc *d_desc, const DdScratch &d, const uint64_t *hex, const uint64_t *ob,
                             uint32_t *err, cudaStream_t st);
+
+// Batches (batch.cu): per-sequence parameters of the batched kernels (a), (a').
+struct SeqJob {
+    const void *S;
+    uint64_t n, sigma;
+    uint32_t L, width;
+    uint64_t *hist;   // sigma u64, zeroed
+    uint64_t *hex;    // 2^L + 1
+    uint64_t *ob, *ze;  // 2^L each
+    uint32_t *err;    // the tree's error word
+};
+uint32_t batch_hist_tiles(uint64_t n);
+cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32_t *hist_tile_start,
+                                 uint32_t hist_tiles, const uint32_t *lvl_start, uint32_t total_levels,
+                                 cudaStream_t st);
 
 // Kernel (e): queries.
 cudaError_t launch_access(const TreeDesc *t, const uint64_t *i, uint64_t m, uint32_t *out, cudaStream_t st);

@@ -264,21 +264,22 @@ class Tree:
         return out
 
 
-def build_batch(seqs: list[torch.Tensor], sigmas: list[int], stream=None) -> list[Tree]:
-    """Builds many trees in one batched call (wt_build_batch); waits for them."""
+def build_batch(seqs: list[torch.Tensor], sigmas: list[int], stream=None, wait: bool = True) -> list[Tree]:
+    """Builds many trees in one batched call (wt_build_batch).  With wait,
+    blocks until all are built and raises on the first failed one."""
     lib = load()
     k = len(seqs)
-    ptrs = (C.c_void_p * k)(*[_dptr(s) for s in seqs])
+    ptrs = (C.c_void_p * k)(*[_dptr(s) if s.numel() else None for s in seqs])
     ns = (C.c_uint64 * k)(*[s.numel() for s in seqs])
     sg = (C.c_uint64 * k)(*sigmas)
     ws = (C.c_int * k)(*[s.element_size() for s in seqs])
     out = (C.c_void_p * k)()
     st = lib.wt_build_batch(ptrs, ns, sg, ws, k, out, C.c_void_p(_stream(stream)))
-    trees = [Tree(out[i], seqs[i].numel(), sigmas[i], seqs[i].element_size()) if out[i] else None
-             for i in range(k)]
     _check(st, "wt_build_batch")
-    for t in trees:
-        t.wait()
+    trees = [Tree(out[i], seqs[i].numel(), sigmas[i], seqs[i].element_size()) for i in range(k)]
+    if wait:
+        for t in trees:
+            t.wait()
     return trees
 
 
