@@ -1,0 +1,73 @@
+"""The serving loop (continuous batching): builds admitted under a memory
+budget with eviction, query batches overlapping the builds on another
+stream, and every result equal to what the same request gets alone."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import compare_tree, needs_gpu, to_dev, wt
+from oracle import oracle as O
+from paper_1610_05994_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+
+def test_serving_results_equal_alone():
+    W = wt()
+    from paper_1610_05994_gb300.serve import BuildRequest, Server
+    rng = np.random.default_rng(11)
+    specs = inputs.serving_specs(40, log2_min=10, log2_max=17)
+    seqs = [sp.generate() for sp in specs]
+    srv = Server(budget_bytes=24 << 20, max_batch=8)
+    issued = []  # (query batch, [rid per tree], tidx, op, c, arg)
+    nxt = 0
+    for round_ in range(60):
+        for _ in range(rng.integers(0, 3)):
+            if nxt < len(specs):
+                sp = specs[nxt]
+                srv.submit(BuildRequest(nxt, to_dev(seqs[nxt]), sp.sigma, 0.0))
+                nxt += 1
+        srv.step()
+        res = list(srv.resident.items())
+        if res and round_ % 2 == 0:
+            trees = [v[0] for _, v in res]
+            rids = [rid for rid, _ in res]
+            m = 1024
+            tidx = rng.integers(0, len(trees), m).astype(np.uint32)
+            op = rng.integers(0, 3, m).astype(np.uint8)
+            c = np.zeros(m, np.uint32)
+            arg = np.zeros(m, np.uint64)
+            for q in range(m):
+                S = seqs[rids[tidx[q]]]
+                c[q] = S[rng.integers(0, len(S))]
+                arg[q] = rng.integers(0, len(S) + 2) if op[q] != 2 else rng.integers(0, 40)
+            qb = srv.query(trees, *(torch.from_numpy(x).cuda() for x in (tidx, op, c, arg)))
+            issued.append((qb, rids, tidx, op, c, arg))
+    while nxt < len(specs):
+        srv.submit(BuildRequest(nxt, to_dev(seqs[nxt]), specs[nxt].sigma, 0.0))
+        nxt += 1
+    srv.drain()
+    assert srv.evicted > 0, "the budget should have forced evictions"
+    assert len(srv.finished) == len(specs)
+    # query answers in the mix equal the oracle's answers for each request alone
+    bits = {}
+    for qb, rids, tidx, op, c, arg in issued:
+        got = qb.out.cpu().numpy()
+        for q in range(len(arg)):
+            rid = rids[tidx[q]]
+            S, sigma = seqs[rid], specs[rid].sigma
+            if rid not in bits:
+                bits[rid] = O.build_bits(S, sigma)
+            b = bits[rid]
+            if op[q] == 0:
+                a = O.access(b, len(S), sigma, arg[q:q + 1])[0]
+                want = 2**64 - 1 if a == 0xFFFFFFFF else int(a)
+            elif op[q] == 1:
+                want = int(O.rank(b, len(S), sigma, c[q:q + 1], arg[q:q + 1])[0])
+            else:
+                want = int(O.select(b, len(S), sigma, c[q:q + 1], arg[q:q + 1])[0])
+            assert int(got[q]) == want, (rid, int(op[q]))
+    # trees still resident equal the oracle's (and so a build alone)
+    for rid, (tree, _, req) in list(srv.resident.items()):
+        compare_tree(tree, seqs[rid], specs[rid].sigma, check_dir=False)
+    srv.close()
