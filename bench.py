@@ -12,6 +12,15 @@ mixed access/rank/select queries runs against the two trees.  The metric is
 built symbols per second.  Inputs are larger than L2, so no flush is needed
 between steps.
 
+``--workload batch`` times the batched build instead: 4096 sequences of
+log-uniform length in [2^10, 2^22], alphabets {4, 20, 256, 65536}, uniform or
+Zipf(1.1), built by one wt_build_batch call per step (one CUDA graph), and
+reports its efficiency against the plain single-sequence path.
+``--workload serve`` runs the serving loop: Poisson arrivals of build
+requests at 70% of the measured batched build throughput, continuous
+batching under a 120 GB budget, batches of 2^16 mixed queries against the
+resident trees, and reports p50/p99 build and query latency.
+
 ``--impl reference`` times the CPU oracle instead (single thread, bounded
 sample of the same workload).  Under torchrun every rank builds its own
 replica (weak scaling, no collective on the data path); rank 0 prints.
@@ -58,7 +67,7 @@ def config_for(name: str) -> dict:
                            "dist": w.dist + (f"{w.alpha}" if w.dist == "zipf" else "")} for w in seqs],
             "queries_per_step": QUERIES,
             "l2": "inputs (>= 1 GiB each) larger than the 129 MB L2; no flush"}
-ORACLE_SAMPLE = {"text+dna": 1 << 27, "words": 1 << 24}     # cpu_baseline: 10-30 s of oracle work
+ORACLE_SAMPLE = {"text+dna": 1 << 28, "words": 1 << 24}     # cpu_baseline: 10-30 s of oracle work
 REFERENCE_SAMPLE = {"text+dna": 1 << 26, "words": 1 << 23}  # --impl reference, per step
 
 
@@ -236,7 +245,7 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
 
     wls = WORKLOAD_SETS[args.workload]
-    host = [w.generate() for w in wls]
+    host = [w.generate(min(w.n, 1 << args.size_log2) if args.size_log2 else None) for w in wls]
     sigmas = [w.sigma for w in wls]
     tidx, op, c, arg = make_queries(host, sigmas, QUERIES, 7)
     seq_d = [torch.from_numpy(h).to(dev) for h in host]
@@ -288,7 +297,7 @@ def run_ours(args, ws, rank, local):
         tt = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    syms_rank = sum(w.n for w in wls)
+    syms_rank = sum(h.size for h in host)
     syms = syms_rank * ws
     value = syms / (ms * 1e-3)
 
@@ -333,34 +342,322 @@ def run_ours(args, ws, rank, local):
 
     if rank != 0:
         return
-    peaks = measured_peaks()
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else "fallback (6800 GB/s)"
-    peak = peak or 6800.0
-    dom = max(stats.items(), key=lambda kv: kv[1]["total_ms"]) if stats else (None, None)
-    roofline = None
-    if dom[0]:
-        name, st = dom
-        achieved = st["alg_bytes"] / (st["total_ms"] * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(name),
-                    "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
-                    "avg_launch_ms": st["total_ms"] / st["launches"]}
-    kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps,
-                   "GBps": v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9 if v["total_ms"] > 0 else None}
-               for k, v in stats.items()}
-    launches = sum(v["launches"] for v in stats.values())
+    roofline, kernels, launches = roofline_of(stats, args.steps)
     cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline_sample(args.workload)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype_of(args.workload), "data": "synthetic",
             "config": dict(config_for(args.workload), parallelism=f"replicas{ws}",
-                           variant={0: "auto", 1: "levelwise", 2: "dd"}[args.variant]),
+                           variant={0: "auto", 1: "levelwise", 2: "dd"}[args.variant],
+                           **({"reduced_size_log2": args.size_log2} if args.size_log2 else {})),
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": syms / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
             "gpu_launches": launches, "clocks": clk, "kernels": kernels}
     print(json.dumps(line), flush=True)
+
+
+def roofline_of(stats: dict, steps: int):
+    """Roofline of the kernel with the largest device time, per-kernel
+    figures per step, and the number of library launches, from the library's
+    own launch profile (CUDA events on the launching stream)."""
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else "fallback (6800 GB/s)"
+    peak = peak or 6800.0
+    roofline = None
+    if stats:
+        name, st = max(stats.items(), key=lambda kv: kv[1]["total_ms"])
+        achieved = st["alg_bytes"] / (st["total_ms"] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(name),
+                    "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
+                    "avg_launch_ms": st["total_ms"] / st["launches"]}
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / steps,
+                   "GBps": v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9 if v["total_ms"] > 0 else None}
+               for k, v in stats.items()}
+    return roofline, kernels, sum(v["launches"] for v in stats.values())
+
+
+def _gen_parallel(specs):
+    """Host sequences of many specs, generated on all host cores."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(min(32, os.cpu_count() or 1)) as ex:
+        return list(ex.map(lambda sp: sp.generate(), specs))
+
+
+def _pack_device(host, dev, align=256):
+    """Copies host sequences into one device buffer (each start aligned) and
+    returns typed views of it, one per sequence."""
+    import torch
+    offs, total = [], 0
+    for h in host:
+        offs.append(total)
+        total += (h.nbytes + align - 1) // align * align
+    stage = torch.empty(max(total, 1), dtype=torch.uint8).pin_memory()
+    sv = stage.numpy()
+    for h, o in zip(host, offs):
+        sv[o:o + h.nbytes] = h.view(np.uint8)
+    buf = stage.to(dev)
+    tdt = {1: torch.uint8, 2: torch.uint16, 4: torch.int32}
+    return buf, [buf[o:o + h.nbytes].view(tdt[h.itemsize]) for h, o in zip(host, offs)]
+
+
+BATCH_CLASS_N = 1 << 28
+
+
+def run_batch(args, ws, rank, local):
+    """Batched build of 4096 sequences per step (one wt_build_batch call, one
+    CUDA graph), and the plain path's rate on one 2^28-symbol sequence of each
+    (alphabet, distribution) class, for the efficiency figure."""
+    import torch
+
+    from paper_1610_05994_gb300 import build as B
+    from paper_1610_05994_gb300 import wt as W
+
+    torch.cuda.set_device(local)
+    B.build_library()
+    W.load()
+    dev = torch.device("cuda", local)
+    specs = inputs.batch_specs(4096, base=inputs.SEED_BASE + 4 + 1000 * rank)
+    t_gen = time.perf_counter()
+    host = _gen_parallel(specs)
+    t_gen = time.perf_counter() - t_gen
+    buf, seqs = _pack_device(host, dev)
+    sigmas = [sp.sigma for sp in specs]
+    n_total = sum(sp.n for sp in specs)
+    st = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+
+    def step(keep):
+        trees = W.build_batch(seqs, sigmas, stream=st, wait=False)
+        with torch.cuda.stream(st):
+            for t in keep:
+                t.free()
+        return trees
+
+    keep = []
+    for _ in range(args.warmup):
+        keep = step(keep)
+    for t in keep:
+        t.wait()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    W.profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        keep = step(keep)
+    e1.record(st)
+    torch.cuda.synchronize()
+    stats = W.profile_end()
+    clk = clocks.stop()
+    for t in keep:
+        t.wait()
+        t.free()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = n_total / (ms * 1e-3)
+
+    # End to end: inputs copied from pinned host memory inside the timed region.
+    stage = torch.empty(buf.numel(), dtype=torch.uint8).pin_memory()
+    stage.copy_(buf)
+    keep = []
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    f0.record(st)
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(st):
+            buf.copy_(stage, non_blocking=True)
+        keep = step(keep)
+    f1.record(st)
+    torch.cuda.synchronize()
+    for t in keep:
+        t.wait()
+        t.free()
+    ms_e2e = f0.elapsed_time(f1) / e2e_steps
+    del buf, seqs, stage
+
+    # Plain path per class: sigma x distribution, one 2^28-symbol sequence each.
+    classes = sorted({(sp.sigma, sp.width, sp.dist) for sp in specs})
+    rate = {}
+    for k, (sigma, width, dist) in enumerate(classes):
+        sp = inputs.SeqSpec(BATCH_CLASS_N, sigma, width, dist, 1.1 if dist == "zipf" else 0.0,
+                            inputs.seq_seed(inputs.SEED_BASE + 40, k))
+        S = torch.from_numpy(sp.generate()).to(dev)
+        for _ in range(2):
+            W.Tree.build(S, sigma).free()
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        c0.record()
+        for _ in range(reps):
+            W.Tree.build(S, sigma, wait=False).free()
+        c1.record()
+        torch.cuda.synchronize()
+        rate[(sigma, width, dist)] = BATCH_CLASS_N / (c0.elapsed_time(c1) / reps * 1e-3)
+        del S
+    plain_sec = sum(sp.n / rate[(sp.sigma, sp.width, sp.dist)] for sp in specs)
+    efficiency = plain_sec / (ms * 1e-3)
+    if rank != 0:
+        return
+    roofline, kernels, launches = roofline_of(stats, args.steps)
+    h2d = sum(h.nbytes for h in host)
+    line = {"metric": "batched wavelet-tree build symbols/sec", "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8+u16", "data": "synthetic",
+            "config": {"workload": "batch of 4096 sequences, n log-uniform in [2^10, 2^22], sigma in "
+                                   "{4, 20, 256, 65536} (u8 for sigma <= 256, else u16), uniform or Zipf(1.1)",
+                       "symbols_per_step": n_total, "host_generation_s": t_gen,
+                       "l2": "inputs (2.6 GB) larger than the 129 MB L2; no flush",
+                       "parallelism": f"replicas{ws}"},
+            "batch_efficiency_vs_plain": efficiency,
+            "plain_rate_per_class": {f"sigma={k[0]} w={k[1]} {k[2]}": v for k, v in rate.items()},
+            "roofline": roofline, "cpu_baseline": None,
+            "e2e": {"value": n_total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 0, "ms_per_step": ms_e2e},
+            "gpu_launches": launches, "clocks": clk, "kernels": kernels}
+    print(json.dumps(line), flush=True)
+
+
+SERVE_POOL_N = 1 << 26
+
+
+def run_serve(args, ws, rank, local):
+    """Serving loop: Poisson arrivals of build requests at an offered load of
+    70% of the measured batched build rate, continuous batching under a 120 GB
+    budget, closed-loop batches of 2^16 mixed queries on the resident trees."""
+    import torch
+
+    from paper_1610_05994_gb300 import build as B
+    from paper_1610_05994_gb300 import wt as W
+    from paper_1610_05994_gb300.serve import BuildRequest, Server, percentiles
+
+    torch.cuda.set_device(local)
+    B.build_library()
+    W.load()
+    dev = torch.device("cuda", local)
+    warm, total = 100, 100 + args.requests
+    specs = inputs.serving_specs(total, base=inputs.SEED_BASE + 5 + 1000 * rank)
+    # Request data: slices of one pinned Zipf(1.0) pool per alphabet, at
+    # seeded offsets; each request is copied to the device when it arrives.
+    pools, hists = {}, {}
+    for k, sigma in enumerate((256, 65536)):
+        h = inputs.zipf(SERVE_POOL_N, sigma, 1.0, inputs.seq_seed(inputs.SEED_BASE + 50, k))
+        pools[sigma] = torch.from_numpy(h).pin_memory()
+        hists[sigma] = np.bincount(h, minlength=sigma).astype(np.float64) / SERVE_POOL_N
+    rng = np.random.default_rng(55 + rank)
+    offs = [int(rng.integers(0, SERVE_POOL_N - sp.n + 1)) for sp in specs]
+
+    def arrive(k):
+        sp = specs[k]
+        S = torch.empty(sp.n, dtype=pools[sp.sigma].dtype, device=dev)
+        S.copy_(pools[sp.sigma][offs[k]:offs[k] + sp.n], non_blocking=True)
+        return S
+
+    # Calibration: the batched build rate on 64 requests of this distribution.
+    cal = [arrive(k) for k in range(64)]
+    for _ in range(2):
+        for t in W.build_batch(cal, [specs[k].sigma for k in range(64)]):
+            t.free()
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    for t in W.build_batch(cal, [specs[k].sigma for k in range(64)]):
+        t.free()
+    torch.cuda.synchronize()
+    batch_rate = sum(specs[k].n for k in range(64)) / (time.perf_counter() - c0)
+    del cal
+    mean_n = float(np.mean([sp.n for sp in specs]))
+    lam = 0.7 * batch_rate / mean_n
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, total))
+
+    srv = Server(budget_bytes=120 << 30, max_batch=1024, device=dev)
+    where = {}  # rid -> (sigma, offset, n)
+    qbs = []
+    qrng = np.random.default_rng(77 + rank)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    W.profile_begin()
+    t0 = time.perf_counter()
+    k = 0
+    qb = None
+    while len(srv.finished) < total:
+        now = time.perf_counter() - t0
+        while k < total and arrivals[k] <= now:
+            where[k] = (specs[k].sigma, offs[k], specs[k].n)
+            srv.submit(BuildRequest(k, arrive(k), specs[k].sigma, t0 + arrivals[k]))
+            k += 1
+        srv.step()
+        srv.poll_queries()
+        if srv.resident and (qb is None or qb.done):
+            rids = list(srv.resident)
+            tidx, op, c, arg = _serve_queries(qrng, rids, where, pools, hists, QUERIES)
+            q = [torch.from_numpy(x).to(dev, non_blocking=False) for x in (tidx, op, c, arg)]
+            qb = srv.query([srv.resident[r][0] for r in rids], *q)
+            qb.measured = k > warm
+            qbs.append(qb)
+    srv.drain()
+    t_end = time.perf_counter()
+    stats = W.profile_end()
+    clk = clocks.stop()
+    meas = [r for r in srv.finished if r.rid >= warm]
+    first = min(r.arrival for r in meas)
+    last = max(r.done for r in meas)
+    value = sum(r.n for r in meas) / (last - first)
+    build_lat = [(r.done - r.arrival) * 1e3 for r in meas]
+    q_lat = [(q.done - q.issued) * 1e3 for q in qbs if getattr(q, "measured", False) and q.done]
+    evicted = srv.evicted
+    srv.close()
+    if rank != 0:
+        return
+    roofline, kernels, launches = roofline_of(stats, 1)
+    line = {"metric": "served wavelet-tree build symbols/sec", "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.requests, "warmup": warm, "ms_per_step": (last - first) * 1e3 / len(meas),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8+u16",
+            "data": "synthetic",
+            "config": {"workload": "serving: Poisson build requests, n log-uniform in [2^12, 2^26], sigma in "
+                                   "{256 (u8), 65536 (u16)}, Zipf(1.0); closed-loop batches of 2^16 mixed "
+                                   "access/rank/select queries on resident trees; 120 GB admission budget",
+                       "requests": args.requests, "warmup_requests": warm, "offered_load": 0.7,
+                       "calibrated_batch_rate": batch_rate, "arrival_rate_per_s": lam,
+                       "parallelism": f"replicas{ws}"},
+            "latency_ms": {"build": percentiles(build_lat), "query_batch": percentiles(q_lat)},
+            "queries_per_s": QUERIES * len(q_lat) / (last - first) if q_lat else None,
+            "query_batches": len(q_lat), "build_batches": srv.batches, "evicted": evicted,
+            "wall_s": t_end - t0, "roofline": roofline, "cpu_baseline": None,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": float(np.mean(
+                        [specs[r.rid].n * specs[r.rid].width for r in meas])), "d2h_bytes_per_step": 0,
+                    "note": "the value itself is end to end: request data is copied from pinned host "
+                            "memory after arrival, inside each request's latency"},
+            "gpu_launches": launches, "clocks": clk, "kernels": kernels}
+    print(json.dumps(line), flush=True)
+
+
+def _serve_queries(rng, rids, where, pools, hists, m):
+    """A batch of m mixed queries over the resident trees: uniform tree, op
+    and position; c drawn from the tree's sequence; j within the symbol's
+    expected count."""
+    tidx = rng.integers(0, len(rids), m).astype(np.uint32)
+    op = rng.integers(0, 3, m).astype(np.uint8)
+    sig = np.array([where[r][0] for r in rids], np.int64)[tidx]
+    off = np.array([where[r][1] for r in rids], np.int64)[tidx]
+    n = np.array([where[r][2] for r in rids], np.int64)[tidx]
+    pos = (rng.random(m) * n).astype(np.int64)
+    c = np.zeros(m, np.uint32)
+    cnt = np.zeros(m, np.float64)
+    for sigma, pool in pools.items():
+        sel = sig == sigma
+        c[sel] = pool.numpy()[off[sel] + pos[sel]]
+        cnt[sel] = hists[sigma][c[sel]] * n[sel]
+    i_arg = (rng.random(m) * (n + 1)).astype(np.uint64)
+    j_arg = (1 + np.floor(rng.random(m) * np.maximum(np.floor(cnt), 1))).astype(np.uint64)
+    arg = np.where(op == 2, j_arg, i_arg).astype(np.uint64)
+    return tidx, op, c, arg
 
 
 def _build_from_host(W, pinned, sigma, variant):
@@ -381,19 +678,26 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS), default="text+dna")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + ["batch", "serve"], default="text+dna")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: measured build requests")
+    ap.add_argument("--size-log2", type=int, default=0,
+                    help="profiling aid: cap each sequence at 2^k symbols (the line then names the cap)")
     ap.add_argument("--variant", type=int, choices=[0, 1, 2], default=0,
                     help="0 auto (autotuned), 1 level-wise, 2 dd-direct")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
+        if args.workload in ("batch", "serve"):
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed on the single-sequence "
+                              "workloads only"}), flush=True)
+            return
         run_reference(args, ws, rank)
         return
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        run_ours(args, ws, rank, local)
+        {"batch": run_batch, "serve": run_serve}.get(args.workload, run_ours)(args, ws, rank, local)
     finally:
         if ws > 1:
             import torch.distributed as dist

@@ -29,11 +29,12 @@ from . import wt as W
 @dataclass
 class BuildRequest:
     rid: int
-    S: torch.Tensor          # device symbols (kept alive until the build is done)
+    S: torch.Tensor | None   # device symbols (released once the tree is resident)
     sigma: int
     arrival: float           # host clock (time.perf_counter) when it arrived
     admitted: float = 0.0
     done: float = 0.0
+    n: int = 0
 
 
 @dataclass
@@ -72,6 +73,7 @@ class Server:
         self.last_query_event: torch.cuda.Event | None = None
         self.evicted = 0
         self.built_symbols = 0
+        self.batches = 0
 
     # ---------------------------------------------------------------- builds
     def submit(self, req: BuildRequest) -> None:
@@ -113,6 +115,7 @@ class Server:
         ev = torch.cuda.Event()
         ev.record(self.build_stream)
         self.inflight.append((batch, trees, ev))
+        self.batches += 1
 
     def _retire(self) -> None:
         still = []
@@ -124,9 +127,11 @@ class Server:
             for (req, need), tree in zip(batch, trees):
                 tree.wait()            # raises if this sequence failed
                 req.done = now
+                req.n = req.S.numel()
+                req.S = None           # the build no longer reads it
                 self.finished.append(req)
                 self.resident[req.rid] = (tree, need, req)
-                self.built_symbols += req.S.numel()
+                self.built_symbols += req.n
         self.inflight = still
 
     def step(self) -> None:
