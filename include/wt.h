@@ -12,7 +12,8 @@
  *
  * Conventions shared by every call:
  *   - Symbols are codes in [0, sigma), stored as unsigned integers of
- *     sym_width bytes (1, 2 or 4), little-endian, packed.
+ *     sym_width bytes (1, 2 or 4), little-endian, packed, with the array
+ *     aligned to sym_width bytes (else WT_ERR_ARG).
  *   - Level l of node v holds the symbols s with s >> (L - l) == v; a node
  *     splits on the bit (s >> (L - 1 - l)) & 1, so for sigma not a power of
  *     two some nodes are empty.

@@ -139,6 +139,7 @@ wt_status check_args(const void *S, uint64_t n, uint64_t sigma, int width) {
     if (sigma == 0 || sigma > WT_MAX_SIGMA) return WT_ERR_ARG;
     if (width < 4 && sigma > (1ull << (8 * width))) return WT_ERR_ARG;
     if (n > 0 && S == nullptr) return WT_ERR_ARG;
+    if (n > 0 && reinterpret_cast<uintptr_t>(S) % (uintptr_t)width != 0) return WT_ERR_ARG;  // natural alignment
     if (n >= (1ull << 56)) return WT_ERR_ARG;
     return WT_OK;
 }
@@ -260,23 +261,25 @@ wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t si
     const size_t hist = align256(R ? (size_t)R * sigma * 4 : sigma * 8);
     const size_t hex = align256(((1ull << L) + 1) * 8);
     const size_t tab = need_levels ? align256((1ull << L) * 8) : 0;
-    const size_t status = need_levels ? align256((size_t)L * ntiles * 8) : 0;
-    const size_t tickets = need_levels ? align256((size_t)L * 4) : 0;
-    const size_t zeroed = hist + status + tickets;
+    const size_t counts = need_levels ? align256(lw_counts_bytes(n, width)) : 0;
+    const size_t prefix = need_levels ? align256(lw_prefix_bytes(n, width)) : 0;
+    const size_t zeroed = hist;
     const size_t buf = align256(n * (uint64_t)width);
     const size_t stmp = align256(scan_tmp_bytes(L));
     const size_t jslot = level_job_slot_bytes();
     const int nbuf = need_levels ? (L >= 3 ? 2 : (L == 2 ? 1 : 0)) : 0;
-    sc.bytes = zeroed + hex + 2 * tab + stmp + jslot + nbuf * buf;
+    sc.bytes = zeroed + 2 * counts + prefix + hex + 2 * tab + stmp + jslot + nbuf * buf;
     sc.mem = dev_alloc(A, sc.bytes, st);
     if (!sc.mem) return WT_ERR_OOM;
     char *p = static_cast<char *>(sc.mem);
     sc.b.hist = reinterpret_cast<uint64_t *>(p);
     p += hist;
-    sc.b.status = reinterpret_cast<uint64_t *>(p);
-    p += status;
-    sc.b.tickets = reinterpret_cast<uint32_t *>(p);
-    p += tickets;
+    sc.b.cnt[0] = reinterpret_cast<uint32_t *>(p);
+    p += counts;
+    sc.b.cnt[1] = reinterpret_cast<uint32_t *>(p);
+    p += counts;
+    sc.b.pre = reinterpret_cast<uint64_t *>(p);
+    p += prefix;
     sc.b.hex = reinterpret_cast<uint64_t *>(p);
     p += hex;
     sc.b.ob = reinterpret_cast<uint64_t *>(p);
@@ -325,7 +328,6 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
             ProfScope p(K_NODE_TABLES, 8.0 * 5 * leaves, st);
             WT_CK(launch_node_tables(b.hex, t->L, b.ob, b.ze, st, b.scan_tmp));
         }
-        const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
         const void *cur = S;
         void *bufs[2] = {b.ping, b.pong};
         for (uint32_t l = 0; l < t->L; l++) {
@@ -334,8 +336,8 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
             const double bytes = nw + t->n / 8.0 + t->n / 128.0 + (nxt ? nw : 0.0);
             ProfScope p(K_LEVEL_PASS, bytes, st);
             WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
-                                    &t->d_desc->lv[l].ones, b.status + l * ntiles, b.tickets + l, t->d_err, b.job_slot,
-                                    st));
+                                    &t->d_desc->lv[l].ones, b.cnt[l & 1], b.pre, b.cnt[(l + 1) & 1], l == 0,
+                                    t->d_err, b.job_slot, st));
             cur = nxt;
         }
     }
@@ -560,21 +562,26 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         carve_levels(d, tb + lvl_off[k], n[k], L[k]);
     }
 
-    // ---- scratch: per sequence histogram, node starts, node tables,
-    // look-back words, ping-pong orders; then the batch tables.
+    // ---- scratch: per sequence histogram, node starts, node tables, tile
+    // counts and prefixes, ping-pong orders; then the batch tables.
     struct Off {
-        size_t hist, hex, ob, ze, status, ping, pong;
+        size_t hist, hex, ob, ze, cnt0, cnt1, pre, ping, pong;
     };
     std::vector<Off> so(count);
-    size_t zeroed = 256;  // tickets live in the first 256 bytes
+    size_t zeroed = 0;
     for (uint32_t k = 0; k < count; k++) {
         so[k].hist = zeroed;
         zeroed += align256(sigma[k] * 8);
-        so[k].status = zeroed;
-        zeroed += align256((size_t)L[k] * ceil_div(n[k], lw_tile_elems(width[k])) * 8);
     }
     size_t sbytes = zeroed;
     for (uint32_t k = 0; k < count; k++) {
+        const bool lv = L[k] > 0 && n[k] > 0;
+        so[k].cnt0 = sbytes;
+        sbytes += lv ? align256(lw_counts_bytes(n[k], width[k])) : 0;
+        so[k].cnt1 = sbytes;
+        sbytes += lv ? align256(lw_counts_bytes(n[k], width[k])) : 0;
+        so[k].pre = sbytes;
+        sbytes += lv ? align256(lw_prefix_bytes(n[k], width[k])) : 0;
         const size_t leaves = L[k] ? (1ull << L[k]) : 0;
         so[k].hex = sbytes;
         sbytes += align256((leaves + 1) * 8);
@@ -597,7 +604,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         uint32_t l;
         std::vector<uint32_t> seqs;
         size_t jobs_off, ts_off;  // in the staging tables
-        uint32_t total;
+        uint32_t total, max_tiles;
     };
     std::vector<LaunchPlan> plans;
     for (int c = 0; c < 3; c++)
@@ -609,7 +616,6 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
                 if (wclass(width[k]) == c && L[k] > l && n[k] > 0) P.seqs.push_back(k);
             if (!P.seqs.empty()) plans.push_back(std::move(P));
         }
-    if (plans.size() > 64) return WT_ERR_ARG;  // ticket area holds 64 launches
 
     // Staging layout (same offsets on host and device).
     size_t tbytes = 0;
@@ -679,17 +685,22 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         LevelJob *pj = reinterpret_cast<LevelJob *>(ht + P.jobs_off);
         uint32_t *pts = reinterpret_cast<uint32_t *>(ht + P.ts_off);
         uint32_t tiles = 0;
+        P.max_tiles = 0;
         for (size_t q = 0; q < P.seqs.size(); q++) {
             const uint32_t k = P.seqs[q];
             const uint32_t l = P.l;
             const uint64_t ntk = ceil_div(n[k], lw_tile_elems(width[k]));
             const void *cur = l == 0 ? S[k] : sc + ((l & 1) ? so[k].ping : so[k].pong);
             void *nxt = sc + ((l & 1) ? so[k].pong : so[k].ping);
+            uint32_t *cnt[2] = {reinterpret_cast<uint32_t *>(sc + so[k].cnt0),
+                                reinterpret_cast<uint32_t *>(sc + so[k].cnt1)};
             pj[q] = make_level_job(cur, nxt, n[k], width[k], L[k], l, reinterpret_cast<uint64_t *>(sc + so[k].ob),
                                    reinterpret_cast<uint64_t *>(sc + so[k].ze), hdesc[k].lv[l],
-                                   &d_descs[k].lv[l].ones, reinterpret_cast<uint64_t *>(sc + so[k].status) + l * ntk);
+                                   &d_descs[k].lv[l].ones, cnt[l & 1], reinterpret_cast<uint64_t *>(sc + so[k].pre),
+                                   cnt[(l + 1) & 1]);
             pts[q] = tiles;
             tiles += (uint32_t)ntk;
+            P.max_tiles = std::max(P.max_tiles, (uint32_t)ntk);
         }
         pts[P.seqs.size()] = tiles;
         P.total = tiles;
@@ -710,7 +721,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         if (e != cudaSuccess && r == WT_OK) r = WT_ERR_CUDA;
     };
     if (r == WT_OK) {
-        ck(cudaMemsetAsync(sc, 0, zeroed, st));
+        if (zeroed) ck(cudaMemsetAsync(sc, 0, zeroed, st));
         ck(cudaMemsetAsync(B->d_err, 0, 4, st));
         ck(cudaMemcpyAsync(dt, ht, tbytes, cudaMemcpyHostToDevice, st));
         ck(cudaMemcpyAsync(d_descs, ht + tbytes, sizeof(TreeDesc) * count, cudaMemcpyHostToDevice, st));
@@ -729,7 +740,6 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
                                     reinterpret_cast<const uint32_t *>(dt + hts_off), hist_tiles,
                                     reinterpret_cast<const uint32_t *>(dt + lts_off), total_levels, st));
         }
-        uint32_t *tickets = reinterpret_cast<uint32_t *>(sc);
         for (size_t q = 0; q < plans.size(); q++) {
             const LaunchPlan &P = plans[q];
             double bytes = 0;
@@ -740,7 +750,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
             ProfScope p(K_LEVEL_PASS, bytes, st);
             ck(launch_level_jobs(P.width, P.l, reinterpret_cast<const LevelJob *>(dt + P.jobs_off),
                                  reinterpret_cast<const uint32_t *>(dt + P.ts_off), (uint32_t)P.seqs.size(), P.total,
-                                 tickets + q, B->d_err, st));
+                                 P.max_tiles, P.l == 0, B->d_err, st));
         }
     }
     if (use_graph) {
@@ -1082,25 +1092,29 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
     if (r != WT_OK) return set_last(r);
     const uint32_t L = levels_of(sigma);
     if (l >= L || !Hex || (n > 0 && (!words || !R))) return set_last(WT_ERR_ARG);
+    if (nxt && reinterpret_cast<uintptr_t>(nxt) % (uintptr_t)sym_width != 0) return set_last(WT_ERR_ARG);
     if (n == 0) return set_last(WT_OK);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Allocator A = current_allocator();
     const Shape s = shape_of(n);
-    const uint64_t ntiles = ceil_div(n, lw_tile_elems(sym_width));
-    // Scratch: node tables, look-back words, ticket, error word, and the
+    // Scratch: error word, tile counts and prefixes, node tables, and the
     // directory parts this entry point does not return (Hy, S1, S0, ones).
     const size_t tab = align256((1ull << L) * 8);
-    const size_t status = align256(ntiles * 8);
-    const size_t zeroed = status + 256;
-    const size_t bytes = zeroed + 2 * tab + s.Hy + 2 * s.S + 256 + level_job_slot_bytes();
+    const size_t counts = align256(lw_counts_bytes(n, sym_width));
+    const size_t prefix = align256(lw_prefix_bytes(n, sym_width));
+    const size_t zeroed = 256;
+    const size_t bytes = zeroed + 2 * counts + prefix + 2 * tab + s.Hy + 2 * s.S + 256 + level_job_slot_bytes();
     void *mem = dev_alloc(A, bytes, st);
     if (!mem) return set_last(WT_ERR_OOM);
     char *p = static_cast<char *>(mem);
-    uint64_t *stw = reinterpret_cast<uint64_t *>(p);
-    p += status;
-    uint32_t *ticket = reinterpret_cast<uint32_t *>(p);
-    uint32_t *err = ticket + 1;
+    uint32_t *err = reinterpret_cast<uint32_t *>(p);
     p += 256;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(p);
+    p += counts;
+    uint32_t *cnt_next = reinterpret_cast<uint32_t *>(p);
+    p += counts;
+    uint64_t *pre = reinterpret_cast<uint64_t *>(p);
+    p += prefix;
     uint64_t *ob = reinterpret_cast<uint64_t *>(p);
     p += tab;
     uint64_t *ze = reinterpret_cast<uint64_t *>(p);
@@ -1121,8 +1135,8 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
     uint32_t herr = 0;
     if (cudaMemsetAsync(mem, 0, zeroed, st) != cudaSuccess ||
         launch_node_tables(Hex, L, ob, ze, st) != cudaSuccess ||
-        launch_level_pass(cur, (l + 1 < L) ? nxt : nullptr, n, sym_width, L, l, ob, ze, lv, ones, stw, ticket, err,
-                          job_slot, st) != cudaSuccess ||
+        launch_level_pass(cur, (l + 1 < L) ? nxt : nullptr, n, sym_width, L, l, ob, ze, lv, ones, cnt, pre, cnt_next,
+                          true, err, job_slot, st) != cudaSuccess ||
         cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
         cudaGetLastError();
         r = WT_ERR_CUDA;

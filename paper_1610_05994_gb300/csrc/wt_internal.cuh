@@ -25,10 +25,6 @@ constexpr uint32_t kBlocksPerSpanMask = (1u << (kSpanShift - 9)) - 1;
 constexpr uint32_t kErrSymbol = 1u;
 constexpr uint32_t kErrTimeout = 2u;
 
-// Bounded spin: a device-side wait gives up after this many polls (each poll
-// sleeps ~0.1-1 us), sets kErrTimeout and lets the kernel finish.
-constexpr uint32_t kMaxSpins = 1u << 22;
-
 struct LevelDesc {
     uint32_t *words;  // ceil(n/512) * 16
     uint32_t *R;      // ceil(n/512) + 1
@@ -56,143 +52,9 @@ __host__ __device__ inline uint32_t levels_of(uint64_t sigma) {
     return L;
 }
 
-// Relaxed 64-bit global accesses for the look-back status words (values only;
-// no data is published through them).
-__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed(uint64_t *p, uint64_t v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    return v;
-}
-
-// Decoupled look-back (Merrill and Garland, 2016) over per-tile counts.
-// Status word: top two bits = flag (1 aggregate, 2 inclusive prefix), low 62
-// bits = value.  Called by all 32 lanes of one warp; returns the exclusive
-// prefix of tile `tile` and publishes its inclusive prefix.  Every wait is
-// bounded: on give-up it ORs kErrTimeout into *err and returns what it has.
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagInc = 2ull << 62;
-constexpr uint64_t kValMask = (1ull << 62) - 1;
-
-__device__ __forceinline__ uint64_t lookback_prefix(uint64_t *status, uint32_t tile, uint64_t agg,
-                                                    uint32_t *err) {
-    const int lane = threadIdx.x & 31;
-    if (tile == 0) {
-        if (lane == 0) st_relaxed(&status[0], kFlagInc | agg);
-        return 0;
-    }
-    if (lane == 0) st_relaxed(&status[tile], kFlagAgg | agg);
-    uint64_t excl = 0;
-    int64_t pos = (int64_t)tile - 1;
-    uint32_t spins = 0;
-    bool gave_up = false;
-    while (true) {
-        const int64_t idx = pos - lane;
-        uint64_t s = (idx >= 0) ? ld_relaxed(&status[idx]) : kFlagInc;
-        while (!__all_sync(0xffffffffu, (s >> 62) != 0)) {
-            if (++spins > kMaxSpins) {
-                gave_up = true;
-                break;
-            }
-            __nanosleep(64);
-            s = (idx >= 0) ? ld_relaxed(&status[idx]) : kFlagInc;
-        }
-        if (gave_up) break;
-        const uint32_t inc_mask = __ballot_sync(0xffffffffu, (s >> 62) == 2);
-        if (inc_mask) {
-            const int first = __ffs(inc_mask) - 1;
-            excl += warp_sum_u64(lane <= first ? (s & kValMask) : 0);
-            break;
-        }
-        excl += warp_sum_u64(s & kValMask);
-        pos -= 32;
-    }
-    if (gave_up && lane == 0) atomicOr(err, kErrTimeout);
-    if (lane == 0) st_relaxed(&status[tile], kFlagInc | (excl + agg));
-    return excl;
-}
-
-// Publishes a tile's own count: the inclusive prefix for tile 0, else the
-// aggregate.  One lane.
-__device__ __forceinline__ void publish_aggregate(uint64_t *status, uint32_t tile, uint64_t agg) {
-    st_relaxed(&status[tile], (tile == 0 ? kFlagInc : kFlagAgg) | agg);
-}
-
-// Decoupled look-back with a 128-tile window, for a tile whose aggregate is
-// already published (publish_aggregate): each lane inspects four
-// predecessors per round, so the chain of inclusive prefixes advances 128
-// tiles per round trip to L2 instead of 32.  Returns the exclusive prefix and
-// publishes the inclusive one; bounded like lookback_prefix.
-__device__ __forceinline__ uint64_t lookback_published(uint64_t *status, uint32_t tile, uint64_t agg, uint32_t *err) {
-    const int lane = threadIdx.x & 31;
-    if (tile == 0) return 0;
-    uint64_t excl = 0;
-    int64_t pos = (int64_t)tile - 1;
-    uint32_t spins = 0;
-    bool gave_up = false;
-    while (true) {
-        uint64_t s[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int64_t idx = pos - (4 * lane + j);
-            s[j] = idx >= 0 ? ld_relaxed(&status[idx]) : kFlagInc;
-        }
-        while (true) {
-            bool ready = true;
-#pragma unroll
-            for (int j = 0; j < 4; j++) ready &= (s[j] >> 62) != 0;
-            if (__all_sync(0xffffffffu, ready)) break;
-            // Give up after kMaxSpins polls, or at once when another CTA has
-            // already given up (its tiles may never be published).
-            if (++spins > kMaxSpins || ((spins & 255u) == 0 && (*(volatile uint32_t *)err & kErrTimeout))) {
-                gave_up = true;
-                break;
-            }
-            __nanosleep(32);
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int64_t idx = pos - (4 * lane + j);
-                if ((s[j] >> 62) == 0) s[j] = ld_relaxed(&status[idx]);
-            }
-        }
-        if (gave_up) break;
-        int jfirst = 4;
-#pragma unroll
-        for (int j = 3; j >= 0; j--)
-            if ((s[j] >> 62) == 2) jfirst = j;
-        const uint32_t inc_lanes = __ballot_sync(0xffffffffu, jfirst < 4);
-        if (inc_lanes) {
-            const int L = __ffs(inc_lanes) - 1;
-            const int jl = __shfl_sync(0xffffffffu, jfirst, L);
-            uint64_t v = 0;
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (lane < L || (lane == L && j <= jl)) v += s[j] & kValMask;
-            excl += warp_sum_u64(v);
-            break;
-        }
-        uint64_t v = 0;
-#pragma unroll
-        for (int j = 0; j < 4; j++) v += s[j] & kValMask;
-        excl += warp_sum_u64(v);
-        pos -= 128;
-    }
-    if (gave_up && lane == 0) atomicOr(err, kErrTimeout);
-    if (lane == 0) st_relaxed(&status[tile], kFlagInc | (excl + agg));
-    return excl;
-}
-
 // ------------------------------------------------------- TMA + mbarrier
 // One-dimensional bulk copies global -> shared (cp.async.bulk) completing on
-// an mbarrier.  Every wait is bounded by kMaxSpins polls.
+// an mbarrier.  Every wait is bounded by kWaitLimitNs of %globaltimer.
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -222,6 +84,19 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, 
             smem_u32(dst_smem)),
         "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Copy only (the caller arms the barrier once for all copies of a phase).
+__device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
 }
 
 // Plain arrival (no transaction), for a phase with nothing to copy.
@@ -268,8 +143,8 @@ struct BuildScratch {
     uint64_t *ze;         // 2^L - 1 : zeros up to each node's end
     uint64_t *scan_tmp;   // scan_tmp_bytes(L)
     void *job_slot;       // level_job_slot_bytes()
-    uint64_t *status;     // L * ntiles look-back words
-    uint32_t *tickets;    // L tile tickets
+    uint32_t *cnt[2];     // tile counts of the level (by level parity), lw_counts_bytes(n, width)
+    uint64_t *pre;        // ones before each tile, lw_prefix_bytes(n, width)
     void *ping;           // n * width
     void *pong;           // n * width
 };
@@ -294,16 +169,17 @@ cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, ui
                                cudaStream_t st, uint64_t *tmp = nullptr);
 size_t scan_tmp_bytes(uint32_t L);
 
-// Kernels (b)+(c): one level pass (level.cu).  status/tickets must be
-// zeroed.  job_slot: level_job_slot_bytes() of device memory.
+// Kernels (b)+(c): the level passes (level.cu).  Level l of a sequence
+// needs the ones of each of its tiles on level l (counted from S for level
+// 0, accumulated by the level-(l-1) pass otherwise); a scan turns them into
+// each tile's prefix, and the pass accumulates the next level's counts.
 uint32_t lw_tile_elems(int width);
+size_t lw_counts_bytes(uint64_t n, int width);   // one level's tile counts (uint32)
+size_t lw_prefix_bytes(uint64_t n, int width);   // tile prefixes (uint64, padded)
 size_t level_job_slot_bytes();
-cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
-                              const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out,
-                              uint64_t *status, uint32_t *ticket, uint32_t *err, void *job_slot, cudaStream_t st);
-// A batch: one launch runs level l of many sequences of one width (level.cu).
+
 // One sequence's share of a level launch (a batch launches many at once).
-struct LevelJob {
+struct __align__(16) LevelJob {
     const void *cur;
     void *nxt;                 // nullptr on the sequence's last level
     uint64_t n, nblocks, nspans;
@@ -312,14 +188,26 @@ struct LevelJob {
     LevelDesc lv;              // its level-l arrays
     uint64_t *ones_out;
     const uint64_t *ob, *ze;   // its level-l node tables
-    uint64_t *status;          // ntiles look-back words
+    uint32_t *cnt;             // ntiles: ones of each tile on level l
+    uint64_t *pre;             // lw_prefix_bytes: ones before each tile (written by the scan)
+    uint32_t *cnt_next;        // ntiles: ones of each tile on level l + 1 (nullptr on the last level)
 };
 
 LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l, const uint64_t *ob,
-                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint64_t *status);
+                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre,
+                        uint32_t *cnt_next);
 size_t level_job_bytes();
+// Level l of every job (all of one width): the tile counts read off P_l
+// when count_cur (level 0, or a pass run on its own), the prefix scan, then
+// the pass.
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
-                              uint32_t total_tiles, uint32_t *ticket, uint32_t *err, cudaStream_t st);
+                              uint32_t total_tiles, uint32_t max_job_tiles, bool count_cur, uint32_t *err,
+                              cudaStream_t st);
+// One sequence (job_slot: level_job_slot_bytes() of device memory).
+cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
+                              const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
+                              uint64_t *pre, uint32_t *cnt_next, bool count_cur, uint32_t *err, void *job_slot,
+                              cudaStream_t st);
 
 // Kernel (d): dd-direct build of all levels for small sigma (dd.cu).
 struct DdScratch {
