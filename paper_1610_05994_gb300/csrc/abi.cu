@@ -268,15 +268,13 @@ wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t si
     const size_t stmp = align256(scan_tmp_bytes(L));
     const size_t jslot = level_job_slot_bytes();
     const int nbuf = need_levels ? (L >= 3 ? 2 : (L == 2 ? 1 : 0)) : 0;
-    sc.bytes = zeroed + 2 * counts + prefix + hex + 2 * tab + stmp + jslot + nbuf * buf;
+    sc.bytes = zeroed + counts + prefix + hex + 2 * tab + stmp + jslot + nbuf * buf;
     sc.mem = dev_alloc(A, sc.bytes, st);
     if (!sc.mem) return WT_ERR_OOM;
     char *p = static_cast<char *>(sc.mem);
     sc.b.hist = reinterpret_cast<uint64_t *>(p);
     p += hist;
-    sc.b.cnt[0] = reinterpret_cast<uint32_t *>(p);
-    p += counts;
-    sc.b.cnt[1] = reinterpret_cast<uint32_t *>(p);
+    sc.b.cnt = reinterpret_cast<uint32_t *>(p);
     p += counts;
     sc.b.pre = reinterpret_cast<uint64_t *>(p);
     p += prefix;
@@ -336,8 +334,7 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
             const double bytes = nw + t->n / 8.0 + t->n / 128.0 + (nxt ? nw : 0.0);
             ProfScope p(K_LEVEL_PASS, bytes, st);
             WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
-                                    &t->d_desc->lv[l].ones, b.cnt[l & 1], b.pre, b.cnt[(l + 1) & 1], l == 0,
-                                    t->d_err, b.job_slot, st));
+                                    &t->d_desc->lv[l].ones, b.cnt, b.pre, t->d_err, b.job_slot, st));
             cur = nxt;
         }
     }
@@ -565,7 +562,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
     // ---- scratch: per sequence histogram, node starts, node tables, tile
     // counts and prefixes, ping-pong orders; then the batch tables.
     struct Off {
-        size_t hist, hex, ob, ze, cnt0, cnt1, pre, ping, pong;
+        size_t hist, hex, ob, ze, cnt, pre, ping, pong;
     };
     std::vector<Off> so(count);
     size_t zeroed = 0;
@@ -576,9 +573,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
     size_t sbytes = zeroed;
     for (uint32_t k = 0; k < count; k++) {
         const bool lv = L[k] > 0 && n[k] > 0;
-        so[k].cnt0 = sbytes;
-        sbytes += lv ? align256(lw_counts_bytes(n[k], width[k])) : 0;
-        so[k].cnt1 = sbytes;
+        so[k].cnt = sbytes;
         sbytes += lv ? align256(lw_counts_bytes(n[k], width[k])) : 0;
         so[k].pre = sbytes;
         sbytes += lv ? align256(lw_prefix_bytes(n[k], width[k])) : 0;
@@ -692,12 +687,10 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
             const uint64_t ntk = ceil_div(n[k], lw_tile_elems(width[k]));
             const void *cur = l == 0 ? S[k] : sc + ((l & 1) ? so[k].ping : so[k].pong);
             void *nxt = sc + ((l & 1) ? so[k].pong : so[k].ping);
-            uint32_t *cnt[2] = {reinterpret_cast<uint32_t *>(sc + so[k].cnt0),
-                                reinterpret_cast<uint32_t *>(sc + so[k].cnt1)};
             pj[q] = make_level_job(cur, nxt, n[k], width[k], L[k], l, reinterpret_cast<uint64_t *>(sc + so[k].ob),
                                    reinterpret_cast<uint64_t *>(sc + so[k].ze), hdesc[k].lv[l],
-                                   &d_descs[k].lv[l].ones, cnt[l & 1], reinterpret_cast<uint64_t *>(sc + so[k].pre),
-                                   cnt[(l + 1) & 1]);
+                                   &d_descs[k].lv[l].ones, reinterpret_cast<uint32_t *>(sc + so[k].cnt),
+                                   reinterpret_cast<uint64_t *>(sc + so[k].pre));
             pts[q] = tiles;
             tiles += (uint32_t)ntk;
             P.max_tiles = std::max(P.max_tiles, (uint32_t)ntk);
@@ -750,7 +743,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
             ProfScope p(K_LEVEL_PASS, bytes, st);
             ck(launch_level_jobs(P.width, P.l, reinterpret_cast<const LevelJob *>(dt + P.jobs_off),
                                  reinterpret_cast<const uint32_t *>(dt + P.ts_off), (uint32_t)P.seqs.size(), P.total,
-                                 P.max_tiles, P.l == 0, B->d_err, st));
+                                 P.max_tiles, B->d_err, st));
         }
     }
     if (use_graph) {
@@ -1103,15 +1096,13 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
     const size_t counts = align256(lw_counts_bytes(n, sym_width));
     const size_t prefix = align256(lw_prefix_bytes(n, sym_width));
     const size_t zeroed = 256;
-    const size_t bytes = zeroed + 2 * counts + prefix + 2 * tab + s.Hy + 2 * s.S + 256 + level_job_slot_bytes();
+    const size_t bytes = zeroed + counts + prefix + 2 * tab + s.Hy + 2 * s.S + 256 + level_job_slot_bytes();
     void *mem = dev_alloc(A, bytes, st);
     if (!mem) return set_last(WT_ERR_OOM);
     char *p = static_cast<char *>(mem);
     uint32_t *err = reinterpret_cast<uint32_t *>(p);
     p += 256;
     uint32_t *cnt = reinterpret_cast<uint32_t *>(p);
-    p += counts;
-    uint32_t *cnt_next = reinterpret_cast<uint32_t *>(p);
     p += counts;
     uint64_t *pre = reinterpret_cast<uint64_t *>(p);
     p += prefix;
@@ -1135,8 +1126,8 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
     uint32_t herr = 0;
     if (cudaMemsetAsync(mem, 0, zeroed, st) != cudaSuccess ||
         launch_node_tables(Hex, L, ob, ze, st) != cudaSuccess ||
-        launch_level_pass(cur, (l + 1 < L) ? nxt : nullptr, n, sym_width, L, l, ob, ze, lv, ones, cnt, pre, cnt_next,
-                          true, err, job_slot, st) != cudaSuccess ||
+        launch_level_pass(cur, (l + 1 < L) ? nxt : nullptr, n, sym_width, L, l, ob, ze, lv, ones, cnt, pre, err,
+                          job_slot, st) != cudaSuccess ||
         cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
         cudaGetLastError();
         r = WT_ERR_CUDA;

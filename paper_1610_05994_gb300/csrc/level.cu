@@ -14,12 +14,12 @@
 //       Section 3.1) written as a closed form of two prefix counts, so one
 //       global scan serves every node of the level.
 //
-// Where the ones before a tile come from: the pass of level l - 1 knows
-// where each symbol lands in P_l and what its level-l bit is, so it adds up
-// the level-l ones of every tile of P_l as it places them (at most four
-// atomic additions per tile); level 0's counts are read off S.  A scan of
-// those counts gives every tile its prefix before its pass starts, so the
-// tiles of a pass are independent: no CTA ever waits for another.
+// Where the ones before a tile come from: a count pass reads P_l at full
+// bandwidth and stores the level-l ones of every tile; a segmented scan
+// turns them into each tile's prefix before the pass starts, so the tiles of
+// a pass are independent and no CTA ever waits for another.  (Counting the
+// next level's ones inside the pass, where each symbol's destination is
+// known, cost more instructions than the extra read.)
 //
 // GPU structure: a persistent CTA of 256 threads takes a contiguous range of
 // tiles and keeps three in flight: one thread issues TMA bulk copies
@@ -61,7 +61,6 @@ struct LwCfg {
     static constexpr int kW = (int)sizeof(Sym);
     static constexpr int kSps = 16 / kW;                              // symbols per 16-byte chunk
     static constexpr uint32_t kTile = kLwTileBytes / kW;              // symbols per tile
-    static constexpr uint32_t kTileShift = kW == 1 ? 13 : (kW == 2 ? 12 : 11);
     static constexpr uint32_t kBlocks = kTile / 512;                  // rank blocks per tile
     static constexpr int kMinCtas = 4;                                // resident CTAs per SM
 };
@@ -135,19 +134,6 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane, uint32_
     return inc - v;
 }
 
-// Ones of hn at the lowest m set bits of x (m <= 16).  Called for the one
-// chunk that a cut between two tiles of the next level passes through, so it
-// is kept out of line: inlined, the compiler would run it for every chunk.
-__device__ __noinline__ uint32_t ones_at_lowest(uint32_t hn, uint32_t x, uint32_t m) {
-    uint32_t r = 0;
-    for (uint32_t j = 0; j < m && x; j++) {
-        const uint32_t b = x & (0u - x);
-        r |= b;
-        x ^= b;
-    }
-    return __popc(hn & r);
-}
-
 __device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
                  "r"(bytes)
@@ -180,8 +166,7 @@ __device__ __forceinline__ void store_run(uintptr_t g0, uint32_t len, const unsi
 
 // ---------------------------------------------------------------- counts
 
-// The ones of every tile read off P_l itself (level 0, where P_0 = S, or a
-// level pass run on its own): symbols with bit L - 1 - l set.
+// The level-l ones of every tile of P_l: symbols with bit L - 1 - l set.
 template <typename Sym>
 __global__ void __launch_bounds__(256) count_kernel(LevelLaunch a) {
     using Cfg = LwCfg<Sym>;
@@ -224,8 +209,7 @@ __global__ void __launch_bounds__(256) count_kernel(LevelLaunch a) {
 // Tile prefixes of every job, pre[t] = ones of the job's tiles before t, in
 // two launches over segments of kScanSeg tiles (CTA x = job * segs + seg):
 // the sums of the segments, then each segment's scan from the sums of the
-// segments before it.  The second also clears the counts the coming pass
-// accumulates.
+// segments before it.
 __global__ void __launch_bounds__(1024) scan_sums_kernel(LevelLaunch a) {
     __shared__ uint32_t part[32];
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
@@ -292,10 +276,7 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     uint64_t run = s_base + s_warp[warp] + inc - sum;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        if (t0 + j < nt) {
-            J.pre[t0 + j] = run;
-            if (J.cnt_next) J.cnt_next[t0 + j] = 0;
-        }
+        if (t0 + j < nt) J.pre[t0 + j] = run;
         run += c[j];
     }
     if (t0 < nt && nt <= t0 + 4) J.pre[nt] = run;  // the total, read with the last tile's pair
@@ -317,7 +298,6 @@ struct LwShared {
     uint64_t bar[kLwStages];               // a stage is in place
     uint32_t wtot[kLwWarps];               // ones of each warp's range
     uint32_t blkw[kLwTileBytes / 512];     // ones before each rank block within its warp's range
-    uint32_t nxt[4];                       // next-level ones: zeros before the cut, all zeros; the same for ones
 };
 
 // Claims this CTA's tile g into stage s (thread 0): the stage record and,
@@ -463,14 +443,11 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     // reused by the next claim).
     unsigned char *const bm_dst = reinterpret_cast<unsigned char *>(J.lv.words) + base / 8;
     const uint32_t bm_bytes = (uint32_t)(min((uint64_t)Cfg::kTile, J.nblocks * 512 - base) / 8);
-    uint32_t *const cnt_next = J.cnt_next;
-    const bool count_next = cnt_next != nullptr;
 
     // Placement.
     bool runs = false;
     uintptr_t gz_b = 0, go_b = 0;
     uint32_t offz = 0, B1 = 0;
-    uint64_t gz = 0, go = 0;
     if (has_next) {
         const uint32_t shv = J.L - l;  // key_l = s >> shv
         const uint32_t nodes = 1u << l;
@@ -478,8 +455,8 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
         const uint32_t kfirst = (uint32_t)sb[0] >> shv, klast = (uint32_t)sb[cnt - 1] >> shv;
         Sym *nxt = static_cast<Sym *>(J.nxt);
         if (kfirst == klast && kfirst < nodes) {
-            gz = (base - P) + __ldg(J.ob + kfirst);  // first zero's position in P_{l+1}
-            go = P + __ldg(J.ze + kfirst);           // first one's position
+            const uint64_t gz = (base - P) + __ldg(J.ob + kfirst);  // first zero's position in P_{l+1}
+            const uint64_t go = P + __ldg(J.ze + kfirst);           // first one's position
             if (gz + Zt > J.n || go + tile_ones > J.n) {
                 bad = true;
             } else {
@@ -488,10 +465,6 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                 go_b = reinterpret_cast<uintptr_t>(nxt + go);
                 offz = (uint32_t)(gz_b & 15);
                 B1 = ((offz + Zt * kW + 15) & ~15u) + (uint32_t)(go_b & 15);
-                // Where the next level's tiles cut the two runs (in ranks).
-                const uint32_t cz = (uint32_t)min((uint64_t)Zt, Cfg::kTile - (gz & (Cfg::kTile - 1)));
-                const uint32_t co = (uint32_t)min((uint64_t)tile_ones, Cfg::kTile - (go & (Cfg::kTile - 1)));
-                uint32_t az = 0, tz = 0, ao = 0, to = 0;  // next-level ones: zeros before cz / all; ones
                 uint32_t stx = 0;  // ones of earlier steps of this warp
 #pragma unroll
                 for (int st = 0; st < kLwSteps; st++) {
@@ -503,7 +476,7 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                     const uint32_t C = offz + B1 + q;
 #pragma unroll
                     for (int kk = 0; kk < kSps; kk++) {
-                        if (q / kW + kk < cnt) {
+                        if (kWhole || q / kW + kk < cnt) {
                             const bool one = (h[st] >> kk) & 1u;
                             const uint32_t at = one ? po : C + kk * kW - po;
                             const uint32_t sv = sym_at<Sym>(x[st], kk);
@@ -512,37 +485,6 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                             if (kW == 4) *reinterpret_cast<uint32_t *>(split + at) = sv;
                             po += one ? kW : 0;
                         }
-                    }
-                    if (count_next) {
-                        // The next level's ones among the chunk's zeros and ones.
-                        const uint32_t hn = chunk_bits<Sym>(x[st], bsh - 1);
-                        const uint32_t nvalid = min((uint32_t)kSps, cnt > q / kW ? cnt - q / kW : 0u);
-                        const uint32_t vmask = (1u << nvalid) - 1u;
-                        const uint32_t zm = ~h[st] & vmask, om = h[st];
-                        const uint32_t z1 = __popc(hn & zm), o1 = __popc(hn & om);
-                        const uint32_t zr = q / kW - o, nz = __popc(zm), no = __popc(om);
-                        tz += z1;
-                        to += o1;
-                        if (zr + nz <= cz)
-                            az += z1;
-                        else if (zr < cz)
-                            az += ones_at_lowest(hn, zm, cz - zr);
-                        if (o + no <= co)
-                            ao += o1;
-                        else if (o < co)
-                            ao += ones_at_lowest(hn, om, co - o);
-                    }
-                }
-                if (count_next) {
-                    az = __reduce_add_sync(0xffffffffu, az);
-                    tz = __reduce_add_sync(0xffffffffu, tz);
-                    ao = __reduce_add_sync(0xffffffffu, ao);
-                    to = __reduce_add_sync(0xffffffffu, to);
-                    if (lane == 0) {
-                        atomicAdd(&sh.nxt[0], az);
-                        atomicAdd(&sh.nxt[1], tz);
-                        atomicAdd(&sh.nxt[2], ao);
-                        atomicAdd(&sh.nxt[3], to);
                     }
                 }
             }
@@ -553,7 +495,6 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                 const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;
                 uint32_t o = wx + stx + ((lpk >> (16 * st)) & 0xffffu);
                 stx += (tpk >> (16 * st)) & 0xffffu;
-                const uint32_t hn = count_next ? chunk_bits<Sym>(x[st], bsh - 1) : 0u;
 #pragma unroll
                 for (int kk = 0; kk < kSps; kk++) {
                     const uint32_t p = q / kW + kk;  // tile position
@@ -566,12 +507,10 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                         continue;
                     }
                     const uint64_t dst = bit ? P + o + __ldg(J.ze + v) : (base + p - P - o) + __ldg(J.ob + v);
-                    if (dst < J.n) {
+                    if (dst < J.n)
                         nxt[dst] = (Sym)sv;
-                        if ((hn >> kk) & 1u) atomicAdd(&cnt_next[dst >> Cfg::kTileShift], 1u);
-                    } else {
+                    else
                         bad = true;
-                    }
                     o += bit;
                 }
             }
@@ -586,16 +525,6 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
             store_run(gz_b, Zt * kW, split + offz, tid);
         else if (tid < 64)
             store_run(go_b, tile_ones * kW, split + B1, tid - 32);
-        else if (tid == 64 && count_next) {
-            // The next level's counts of the tiles the two runs fall in.
-            const uint32_t az = sh.nxt[0], tz = sh.nxt[1], ao = sh.nxt[2], to = sh.nxt[3];
-            sh.nxt[0] = sh.nxt[1] = sh.nxt[2] = sh.nxt[3] = 0;
-            const uint64_t dz = gz >> Cfg::kTileShift, dq = go >> Cfg::kTileShift;
-            if (az) atomicAdd(&cnt_next[dz], az);
-            if (tz - az) atomicAdd(&cnt_next[dz + 1], tz - az);
-            if (ao) atomicAdd(&cnt_next[dq], ao);
-            if (to - ao) atomicAdd(&cnt_next[dq + 1], to - ao);
-        }
     }
 }
 
@@ -617,7 +546,6 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
     bool have_job = false;
     if (tid == 0) {
         for (int s = 0; s < kLwStages; s++) mbar_init(&sh.bar[s], 1);
-        for (int j = 0; j < 4; j++) sh.nxt[j] = 0;
         fence_mbar_init();
         if (g_begin < g_end) k = find_job(a, g_begin);
         for (int s = 0; s < kLwStages; s++) lw_claim<Sym>(a, sh, in, s, g_begin + s, g_end, k, have_job);
@@ -665,7 +593,7 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
 constexpr size_t kLwSmem = kLwStages * kLwTileBytes + 2 * kLwSplitBytes + 2 * kLwBitsBytes + sizeof(LwShared);
 
 template <typename Sym>
-static cudaError_t launch_lw(const LevelLaunch &a, bool count_cur, cudaStream_t st) {
+static cudaError_t launch_lw(const LevelLaunch &a, cudaStream_t st) {
     // Persistent grid: every resident CTA slot, at most one CTA per tile.
     static int slots = 0, sms = 0;
     if (!slots) {
@@ -684,10 +612,8 @@ static cudaError_t launch_lw(const LevelLaunch &a, bool count_cur, cudaStream_t 
         }
         slots = sms * per_sm;
     }
-    if (count_cur) {
-        const uint32_t g0 = a.total_tiles < (uint32_t)(sms * 8) ? a.total_tiles : (uint32_t)(sms * 8);
-        count_kernel<Sym><<<g0, 256, 0, st>>>(a);
-    }
+    const uint32_t g0 = a.total_tiles < (uint32_t)(sms * 8) ? a.total_tiles : (uint32_t)(sms * 8);
+    count_kernel<Sym><<<g0, 256, 0, st>>>(a);
     scan_sums_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
     scan_segs_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
     const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
@@ -696,8 +622,7 @@ static cudaError_t launch_lw(const LevelLaunch &a, bool count_cur, cudaStream_t 
 }
 
 LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l, const uint64_t *ob,
-                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre,
-                        uint32_t *cnt_next) {
+                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre) {
     LevelJob j;
     j.cur = cur;
     j.nxt = (l + 1 < L) ? nxt : nullptr;
@@ -712,13 +637,11 @@ LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint3
     j.ze = ze + ((1ull << l) - 1);
     j.cnt = cnt;
     j.pre = pre;
-    j.cnt_next = (l + 1 < L) ? cnt_next : nullptr;
     return j;
 }
 
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
-                              uint32_t total_tiles, uint32_t max_job_tiles, bool count_cur, uint32_t *err,
-                              cudaStream_t st) {
+                              uint32_t total_tiles, uint32_t max_job_tiles, uint32_t *err, cudaStream_t st) {
     if (njobs == 0 || total_tiles == 0) return cudaSuccess;
     LevelLaunch a;
     a.jobs = jobs;
@@ -729,9 +652,9 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.segs = (uint32_t)ceil_div(max_job_tiles ? max_job_tiles : 1, kScanSeg);
     a.err = err;
     switch (width) {
-        case 1: return launch_lw<uint8_t>(a, count_cur, st);
-        case 2: return launch_lw<uint16_t>(a, count_cur, st);
-        case 4: return launch_lw<uint32_t>(a, count_cur, st);
+        case 1: return launch_lw<uint8_t>(a, st);
+        case 2: return launch_lw<uint16_t>(a, st);
+        case 4: return launch_lw<uint32_t>(a, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -750,16 +673,15 @@ size_t level_job_slot_bytes() { return (sizeof(LevelJob) + 2 * sizeof(uint32_t) 
 
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
-                              uint64_t *pre, uint32_t *cnt_next, bool count_cur, uint32_t *err, void *job_slot,
-                              cudaStream_t st) {
+                              uint64_t *pre, uint32_t *err, void *job_slot, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, cnt, pre, cnt_next);
+    const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, cnt, pre);
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
     uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
     put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, count_cur, err, st);
+    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, err, st);
 }
 
 }  // namespace wt

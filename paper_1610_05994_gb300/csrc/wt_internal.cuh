@@ -143,7 +143,7 @@ struct BuildScratch {
     uint64_t *ze;         // 2^L - 1 : zeros up to each node's end
     uint64_t *scan_tmp;   // scan_tmp_bytes(L)
     void *job_slot;       // level_job_slot_bytes()
-    uint32_t *cnt[2];     // tile counts of the level (by level parity), lw_counts_bytes(n, width)
+    uint32_t *cnt;        // tile counts of a level, lw_counts_bytes(n, width)
     uint64_t *pre;        // ones before each tile, lw_prefix_bytes(n, width)
     void *ping;           // n * width
     void *pong;           // n * width
@@ -169,13 +169,12 @@ cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, ui
                                cudaStream_t st, uint64_t *tmp = nullptr);
 size_t scan_tmp_bytes(uint32_t L);
 
-// Kernels (b)+(c): the level passes (level.cu).  Level l of a sequence
-// needs the ones of each of its tiles on level l (counted from S for level
-// 0, accumulated by the level-(l-1) pass otherwise); a scan turns them into
-// each tile's prefix, and the pass accumulates the next level's counts.
+// Kernels (b)+(c): the level passes (level.cu).  Each level: a count pass
+// stores the level-l ones of every tile of P_l, a scan turns them into each
+// tile's prefix, and the pass writes the level and places P_{l+1}.
 uint32_t lw_tile_elems(int width);
-size_t lw_counts_bytes(uint64_t n, int width);   // one level's tile counts (uint32)
-size_t lw_prefix_bytes(uint64_t n, int width);   // tile prefixes (uint64, padded)
+size_t lw_counts_bytes(uint64_t n, int width);   // tile counts (uint32)
+size_t lw_prefix_bytes(uint64_t n, int width);   // tile prefixes (uint64, padded) and scan sums
 size_t level_job_slot_bytes();
 
 // One sequence's share of a level launch (a batch launches many at once).
@@ -189,25 +188,20 @@ struct __align__(16) LevelJob {
     uint64_t *ones_out;
     const uint64_t *ob, *ze;   // its level-l node tables
     uint32_t *cnt;             // ntiles: ones of each tile on level l
-    uint64_t *pre;             // lw_prefix_bytes: ones before each tile (written by the scan)
-    uint32_t *cnt_next;        // ntiles: ones of each tile on level l + 1 (nullptr on the last level)
+    uint64_t *pre;             // lw_prefix_bytes: ones before each tile
 };
 
 LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l, const uint64_t *ob,
-                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre,
-                        uint32_t *cnt_next);
+                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre);
 size_t level_job_bytes();
-// Level l of every job (all of one width): the tile counts read off P_l
-// when count_cur (level 0, or a pass run on its own), the prefix scan, then
-// the pass.
+// Level l of every job (all of one width): counts, prefix scan, pass.
+// max_job_tiles: the most tiles of any one job.
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
-                              uint32_t total_tiles, uint32_t max_job_tiles, bool count_cur, uint32_t *err,
-                              cudaStream_t st);
+                              uint32_t total_tiles, uint32_t max_job_tiles, uint32_t *err, cudaStream_t st);
 // One sequence (job_slot: level_job_slot_bytes() of device memory).
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
-                              uint64_t *pre, uint32_t *cnt_next, bool count_cur, uint32_t *err, void *job_slot,
-                              cudaStream_t st);
+                              uint64_t *pre, uint32_t *err, void *job_slot, cudaStream_t st);
 
 // Kernel (d): dd-direct build of all levels for small sigma (dd.cu).
 struct DdScratch {
