@@ -618,6 +618,8 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
     tbytes += align256(sizeof(SeqJob) * count);
     const size_t hts_off = tbytes;
     tbytes += align256(4 * ((size_t)count + 1));
+    const size_t sls_off = tbytes;
+    tbytes += align256(4 * ((size_t)count + 1));
     const size_t lts_off = tbytes;
     tbytes += align256(4 * ((size_t)count + 1));
     for (auto &P : plans) {
@@ -656,7 +658,8 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
     SeqJob *hjobs = reinterpret_cast<SeqJob *>(ht + seqjob_off);
     uint32_t *hts = reinterpret_cast<uint32_t *>(ht + hts_off);
     uint32_t *lts = reinterpret_cast<uint32_t *>(ht + lts_off);
-    uint32_t hist_tiles = 0, total_levels = 0;
+    uint32_t *sls = reinterpret_cast<uint32_t *>(ht + sls_off);
+    uint32_t hist_tiles = 0, hist_slabs = 0, total_levels = 0;
     for (uint32_t k = 0; k < count; k++) {
         SeqJob &J = hjobs[k];
         J.S = S[k];
@@ -670,11 +673,14 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         J.ze = reinterpret_cast<uint64_t *>(sc + so[k].ze);
         J.err = d_errs + k;
         hts[k] = hist_tiles;
-        hist_tiles += batch_hist_tiles(n[k]);
+        hist_tiles += batch_hist_tiles(n[k], sigma[k]);
+        sls[k] = hist_slabs;
+        hist_slabs += batch_hist_slabs(n[k], sigma[k]);
         lts[k] = total_levels;
         total_levels += L[k];
     }
     hts[count] = hist_tiles;
+    sls[count] = hist_slabs;
     lts[count] = total_levels;
     for (auto &P : plans) {
         LevelJob *pj = reinterpret_cast<LevelJob *>(ht + P.jobs_off);
@@ -731,6 +737,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
             ProfScope p(K_HIST, nw, st);
             ck(launch_batch_prepare(reinterpret_cast<const SeqJob *>(dt + seqjob_off), count,
                                     reinterpret_cast<const uint32_t *>(dt + hts_off), hist_tiles,
+                                    reinterpret_cast<const uint32_t *>(dt + sls_off), hist_slabs,
                                     reinterpret_cast<const uint32_t *>(dt + lts_off), total_levels, st));
         }
         for (size_t q = 0; q < plans.size(); q++) {

@@ -15,7 +15,15 @@ constexpr int kBatchThreads = 512;
 constexpr uint32_t kBatchHistTile = 16384;   // symbols per histogram CTA
 constexpr uint32_t kBatchSmemBins = 8192;    // alphabets up to this use a shared-memory histogram
 
-uint32_t batch_hist_tiles(uint64_t n) { return (uint32_t)ceil_div(n, kBatchHistTile); }
+constexpr uint64_t kBatchSlab = 1ull << 20;   // symbols per packed-histogram CTA
+
+static bool packed_class(uint64_t sigma) { return sigma > kBatchSmemBins && sigma <= kPackedMaxSigma; }
+uint32_t batch_hist_tiles(uint64_t n, uint64_t sigma) {
+    return packed_class(sigma) ? 0u : (uint32_t)ceil_div(n, kBatchHistTile);
+}
+uint32_t batch_hist_slabs(uint64_t n, uint64_t sigma) {
+    return packed_class(sigma) ? (uint32_t)ceil_div(n, kBatchSlab) : 0u;
+}
 
 // Index of the largest start[k] <= x among k < count (start nondecreasing, start[0] = 0).
 __device__ __forceinline__ uint32_t find_seq(const uint32_t *start, uint32_t count, uint32_t x) {
@@ -42,7 +50,8 @@ __global__ void batch_clear_err_kernel(const SeqJob *__restrict__ jobs, uint32_t
     if (k < nseq) *jobs[k].err = 0;
 }
 
-// Leaf histogram of every sequence: CTA b takes one tile of one sequence.
+// Leaf histogram of the sequences with small (or very large) alphabets:
+// CTA b takes one tile of one sequence.
 __global__ void __launch_bounds__(kBatchThreads) batch_hist_kernel(const SeqJob *__restrict__ jobs,
                                                                    const uint32_t *__restrict__ tile_start,
                                                                    uint32_t nseq) {
@@ -53,8 +62,14 @@ __global__ void __launch_bounds__(kBatchThreads) batch_hist_kernel(const SeqJob 
     if (base >= J.n) return;
     const uint32_t m = (uint32_t)((J.n - base) < kBatchHistTile ? (J.n - base) : kBatchHistTile);
     const bool shared_bins = J.sigma <= kBatchSmemBins;
+    // Small alphabets: one private copy of the bins per warp (up to all
+    // warps), so the warps of a CTA do not queue on the same few words.
+    const uint32_t sig = (uint32_t)J.sigma;
+    uint32_t copies = shared_bins ? kBatchSmemBins / sig : 1;
+    if (copies > kBatchThreads / 32) copies = kBatchThreads / 32;
+    uint32_t *mine = bins + ((threadIdx.x >> 5) % copies) * sig;
     if (shared_bins)
-        for (uint32_t c = threadIdx.x; c < J.sigma; c += blockDim.x) bins[c] = 0;
+        for (uint32_t c = threadIdx.x; c < sig * copies; c += blockDim.x) bins[c] = 0;
     __syncthreads();
     bool bad = false;
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
@@ -62,16 +77,40 @@ __global__ void __launch_bounds__(kBatchThreads) batch_hist_kernel(const SeqJob 
         if ((uint64_t)s >= J.sigma)
             bad = true;
         else if (shared_bins)
-            atomicAdd(&bins[s], 1u);
+            atomicAdd(&mine[s], 1u);
         else
             atomicAdd(reinterpret_cast<unsigned long long *>(&J.hist[s]), 1ull);
     }
     if (bad) atomicOr(J.err, kErrSymbol);
     if (shared_bins) {
         __syncthreads();
-        for (uint32_t c = threadIdx.x; c < J.sigma; c += blockDim.x)
-            if (bins[c]) atomicAdd(reinterpret_cast<unsigned long long *>(&J.hist[c]), (unsigned long long)bins[c]);
+        for (uint32_t c = threadIdx.x; c < sig; c += blockDim.x) {
+            uint32_t sum = 0;
+            for (uint32_t q = 0; q < copies; q++) sum += bins[q * sig + c];
+            if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&J.hist[c]), (unsigned long long)sum);
+        }
     }
+}
+
+// Leaf histogram of the sequences with mid-size alphabets (packed 16-bit
+// shared bins): CTA b takes one slab of kBatchSlab symbols of one sequence.
+__global__ void __launch_bounds__(kPackedThreads) batch_hist_packed_kernel(const SeqJob *__restrict__ jobs,
+                                                                          const uint32_t *__restrict__ slab_start,
+                                                                          uint32_t nseq) {
+    extern __shared__ uint32_t w[];
+    const uint32_t k = find_seq(slab_start, nseq, blockIdx.x);
+    const SeqJob &J = jobs[k];
+    const uint32_t sigma = (uint32_t)J.sigma;
+    for (uint32_t j = threadIdx.x; j < (sigma + 1) / 2; j += blockDim.x) w[j] = 0;
+    __syncthreads();
+    const uint64_t begin = (uint64_t)(blockIdx.x - slab_start[k]) * kBatchSlab;
+    const uint64_t end = begin + kBatchSlab < J.n ? begin + kBatchSlab : J.n;
+    bool bad = false;
+    if (J.width == 2)
+        packed_count<uint16_t>(static_cast<const uint16_t *>(J.S), begin, end, sigma, w, J.hist, bad);
+    else
+        packed_count<uint32_t>(static_cast<const uint32_t *>(J.S), begin, end, sigma, w, J.hist, bad);
+    if (bad) atomicOr(J.err, kErrSymbol);
 }
 
 // Exclusive scan of one CTA's per-thread values.
@@ -151,11 +190,22 @@ __global__ void __launch_bounds__(kBatchThreads) batch_tables_kernel(const SeqJo
 }
 
 cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32_t *hist_tile_start,
-                                 uint32_t hist_tiles, const uint32_t *lvl_start, uint32_t total_levels,
-                                 cudaStream_t st) {
+                                 uint32_t hist_tiles, const uint32_t *slab_start, uint32_t slabs,
+                                 const uint32_t *lvl_start, uint32_t total_levels, cudaStream_t st) {
     if (nseq == 0) return cudaSuccess;
     batch_clear_err_kernel<<<(nseq + 255) / 256, 256, 0, st>>>(jobs, nseq);
     if (hist_tiles) batch_hist_kernel<<<hist_tiles, kBatchThreads, 0, st>>>(jobs, hist_tile_start, nseq);
+    if (slabs) {
+        const size_t smem = (kPackedMaxSigma / 2) * sizeof(uint32_t);
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(batch_hist_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        batch_hist_packed_kernel<<<slabs, kPackedThreads, smem, st>>>(jobs, slab_start, nseq);
+    }
     batch_starts_kernel<<<nseq, kBatchThreads, 0, st>>>(jobs);
     if (total_levels) batch_tables_kernel<<<total_levels, kBatchThreads, 0, st>>>(jobs, lvl_start, nseq);
     return cudaGetLastError();

@@ -115,8 +115,25 @@ __global__ void __launch_bounds__(kHistThreads) hist_replicated_kernel(const Sym
     if (bad) atomicOr(err, kErrSymbol);
 }
 
+// Mid-size alphabets: packed 16-bit shared bins (one CTA per SM, a
+// contiguous slab of S each).
+template <typename Sym>
+__global__ void __launch_bounds__(kPackedThreads) hist_packed_kernel(const Sym *__restrict__ S, uint64_t n,
+                                                                    uint32_t sigma, uint64_t slab,
+                                                                    uint64_t *__restrict__ hist,
+                                                                    uint32_t *__restrict__ err) {
+    extern __shared__ uint32_t w[];
+    for (uint32_t j = threadIdx.x; j < (sigma + 1) / 2; j += blockDim.x) w[j] = 0;
+    __syncthreads();
+    const uint64_t begin = blockIdx.x * slab;
+    const uint64_t end = begin + slab < n ? begin + slab : n;
+    bool bad = false;
+    if (begin < end) packed_count<Sym>(S, begin, end, sigma, w, hist, bad);
+    if (bad) atomicOr(err, kErrSymbol);
+}
+
 uint32_t hist_replicas(uint64_t n, uint64_t sigma) {
-    if (sigma <= kHistSmemBins || n >= (1ull << 32)) return 0;  // not this path
+    if (sigma <= kPackedMaxSigma || n >= (1ull << 32)) return 0;  // not this path
     uint64_t R = (64ull << 20) / (sigma * 4);                     // at most 64 MB of counters
     if (R > 16) R = 16;
     return R < 1 ? 1 : (uint32_t)R;
@@ -168,6 +185,19 @@ static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64
                                              (int)smem);
         if (e != cudaSuccess) return e;
         hist_shared_kernel<Sym><<<(unsigned)grid, kHistThreads, smem, st>>>(s, n, sig, copies, hist, err);
+    } else if (sigma <= kPackedMaxSigma) {
+        const size_t smem = (kPackedMaxSigma / 2) * sizeof(uint32_t);
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(hist_packed_kernel<Sym>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const uint64_t g = (uint64_t)sm_count();
+        const uint64_t slab = ceil_div(n, g);
+        hist_packed_kernel<Sym><<<(unsigned)ceil_div(n, slab), kPackedThreads, smem, st>>>(s, n, (uint32_t)sigma, slab,
+                                                                                         hist, err);
     } else {
         hist_global_kernel<Sym><<<(unsigned)grid, kHistThreads, 0, st>>>(s, n, sigma, hist, err);
     }

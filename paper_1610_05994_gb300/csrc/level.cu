@@ -22,9 +22,10 @@
 // known, cost more instructions than the extra read.)
 //
 // GPU structure: a persistent CTA of 256 threads takes a contiguous range of
-// tiles and keeps three in flight: one thread issues TMA bulk copies
-// (cp.async.bulk) of the symbols and of the tile's prefix into a
-// shared-memory stage two tiles ahead.  Per tile:
+// tiles and keeps four stages: warp 0 claims a tile three ahead and one
+// thread issues TMA bulk copies (cp.async.bulk) of its symbols and of its
+// prefix into a shared-memory stage while the CTA works on the current one.
+// Per tile:
 //   * a lane owns 16 consecutive bytes of each 512-byte warp step, so its
 //     level bits are 16 (8, 4) consecutive bits of the bitmap: they go to a
 //     shared-memory copy of the tile's bitmap that leaves with one bulk
@@ -53,7 +54,7 @@ constexpr uint32_t kLwWarpBytes = 512 * kLwSteps;                  // a warp's r
 constexpr uint32_t kLwTileBytes = kLwWarpBytes * kLwWarps;         // 8 KB
 constexpr uint32_t kLwSplitBytes = kLwTileBytes + 64;              // two runs + alignment slack
 constexpr uint32_t kLwBitsBytes = kLwTileBytes / 8;                // the bitmap copy (for bytes)
-constexpr int kLwStages = 3;
+constexpr int kLwStages = 4;
 constexpr uint32_t kNoTile = 0xffffffffu;
 
 template <typename Sym>
@@ -300,17 +301,22 @@ struct LwShared {
     uint32_t blkw[kLwTileBytes / 512];     // ones before each rank block within its warp's range
 };
 
-// Claims this CTA's tile g into stage s (thread 0): the stage record and,
-// by bulk copy, the prefix pair and (whole aligned tiles) the symbols.
+// Claims this CTA's tile g into stage s (warp 0, all lanes): the stage
+// record (copied by the lanes) and, by bulk copy, the prefix pair and (whole
+// aligned tiles) the symbols.  k and have_job are the same in every lane.
 template <typename Sym>
 __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, unsigned char *in, int s, uint32_t g,
                                          uint32_t g_end, uint32_t &k, bool &have_job) {
     using Cfg = LwCfg<Sym>;
+    constexpr int kJobWords = (int)(sizeof(LevelJob) / 8);
+    const int lane = threadIdx.x & 31;
     LwStage &S = sh.st[s];
     if (g >= g_end) {
-        S.tile = kNoTile;
-        S.full = 0;
-        mbar_arrive(&sh.bar[s]);
+        if (lane == 0) {
+            S.tile = kNoTile;
+            S.full = 0;
+            mbar_arrive(&sh.bar[s]);
+        }
         return;
     }
     while (k + 1 < a.njobs && a.tile_start[k + 1] <= g) {
@@ -318,20 +324,25 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
         have_job = false;
     }
     if (!have_job) {
-        sh.job = a.jobs[k];
+        if (lane < kJobWords)
+            reinterpret_cast<uint64_t *>(&sh.job)[lane] = reinterpret_cast<const uint64_t *>(a.jobs + k)[lane];
         have_job = true;
+        __syncwarp();
     }
-    S.J = sh.job;
-    const uint32_t tile = g - a.tile_start[k];
-    const uint64_t base = (uint64_t)tile * Cfg::kTile;
-    const bool full = S.J.n - base >= Cfg::kTile && (reinterpret_cast<uintptr_t>(S.J.cur) & 15) == 0;
-    S.tile = tile;
-    S.full = full;
-    fence_proxy_async_smem();
-    mbar_arrive_expect(&sh.bar[s], 16 + (full ? kLwTileBytes : 0));
-    bulk_copy(S.pre2, S.J.pre + (tile & ~1u), 16, &sh.bar[s]);
-    if (full)
-        bulk_copy(in + s * kLwTileBytes, static_cast<const Sym *>(S.J.cur) + base, kLwTileBytes, &sh.bar[s]);
+    if (lane < kJobWords) reinterpret_cast<uint64_t *>(&S.J)[lane] = reinterpret_cast<const uint64_t *>(&sh.job)[lane];
+    __syncwarp();
+    if (lane == 0) {
+        const uint32_t tile = g - a.tile_start[k];
+        const uint64_t base = (uint64_t)tile * Cfg::kTile;
+        const bool full = S.J.n - base >= Cfg::kTile && (reinterpret_cast<uintptr_t>(S.J.cur) & 15) == 0;
+        S.tile = tile;
+        S.full = full;
+        fence_proxy_async_smem();
+        mbar_arrive_expect(&sh.bar[s], 16 + (full ? kLwTileBytes : 0));
+        bulk_copy(S.pre2, S.J.pre + (tile & ~1u), 16, &sh.bar[s]);
+        if (full)
+            bulk_copy(in + s * kLwTileBytes, static_cast<const Sym *>(S.J.cur) + base, kLwTileBytes, &sh.bar[s]);
+    }
 }
 
 // One tile: count, directory, placement and the bulk stores (all threads).
@@ -547,8 +558,11 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
     if (tid == 0) {
         for (int s = 0; s < kLwStages; s++) mbar_init(&sh.bar[s], 1);
         fence_mbar_init();
+    }
+    __syncwarp();
+    if (tid < 32) {
         if (g_begin < g_end) k = find_job(a, g_begin);
-        for (int s = 0; s < kLwStages; s++) lw_claim<Sym>(a, sh, in, s, g_begin + s, g_end, k, have_job);
+        for (int s = 0; s < kLwStages - 1; s++) lw_claim<Sym>(a, sh, in, s, g_begin + s, g_end, k, have_job);
     }
     __syncthreads();
 
@@ -562,6 +576,11 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
             break;
         }
         if (S.tile == kNoTile) break;  // every thread reads the same record
+        // Stage (i + 3) % 4 held tile i - 1, which is done: claim tile i + 3
+        // into it while the other warps count this one.
+        if (tid < 32)
+            lw_claim<Sym>(a, sh, in, (int)((i + kLwStages - 1) % kLwStages), g_begin + i + kLwStages - 1, g_end, k,
+                          have_job);
         const LevelJob &J = S.J;
         unsigned char *buf = in + s * kLwTileBytes;
         unsigned char *split = split_base + par * kLwSplitBytes;
@@ -582,8 +601,6 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
         else
             lw_tile<Sym, false>(a, S, sh, buf, split, bits, bad);
         if (tid == 0 || tid == 32) bulk_commit();
-        // Stage s is free: claim this CTA's tile i + kLwStages into it.
-        if (tid == 0) lw_claim<Sym>(a, sh, in, s, g_begin + i + kLwStages, g_end, k, have_job);
     }
     if (tid == 0 || tid == 32) bulk_wait_all();
     if (failed && tid == 0) atomicOr(a.err, kErrTimeout);

@@ -133,6 +133,47 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
     return false;
 }
 
+// ------------------------------------------------------ packed histogram
+// Alphabets too large for 32-bit shared bins: 16-bit bins, two per shared
+// word.  A bin that reaches 2^15 hands 2^15 to the global histogram at once,
+// so a half-word never carries into its neighbour (fewer than 2^15 further
+// additions can land before the hand-over, one per thread at most).
+constexpr uint32_t kPackedMaxSigma = 96 * 1024;       // 192 KB of shared words
+constexpr uint32_t kPackedThreads = 1024;
+
+__device__ __forceinline__ void packed_add(uint32_t *w, uint64_t *hist, uint32_t s) {
+    const uint32_t sh = 16 * (s & 1);
+    const uint32_t old = atomicAdd(&w[s >> 1], 1u << sh);
+    if (((old >> sh) & 0xffffu) == 0x7fffu) {
+        atomicSub(&w[s >> 1], 0x8000u << sh);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&hist[s]), 0x8000ull);
+    }
+}
+
+// Counts S[begin, end) (all threads of the CTA) into the shared words w
+// (zeroed), then adds them to hist and clears w again.  Returns (in bad)
+// whether a symbol was >= sigma.
+template <typename Sym>
+__device__ __forceinline__ void packed_count(const Sym *__restrict__ S, uint64_t begin, uint64_t end, uint32_t sigma,
+                                             uint32_t *w, uint64_t *hist, bool &bad) {
+    for (uint64_t k = begin + threadIdx.x; k < end; k += blockDim.x) {
+        const uint32_t s = (uint32_t)S[k];
+        if (s < sigma)
+            packed_add(w, hist, s);
+        else
+            bad = true;
+    }
+    __syncthreads();
+    const uint32_t words = (sigma + 1) / 2;
+    for (uint32_t j = threadIdx.x; j < words; j += blockDim.x) {
+        const uint32_t v = w[j];
+        if (v & 0xffffu) atomicAdd(reinterpret_cast<unsigned long long *>(&hist[2 * j]), (unsigned long long)(v & 0xffffu));
+        if (v >> 16) atomicAdd(reinterpret_cast<unsigned long long *>(&hist[2 * j + 1]), (unsigned long long)(v >> 16));
+        w[j] = 0;
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------ launchers
 // (defined in build.cu / query.cu, called from abi.cu)
 
@@ -232,10 +273,13 @@ struct SeqJob {
     uint64_t *ob, *ze;  // 2^L each
     uint32_t *err;    // the tree's error word
 };
-uint32_t batch_hist_tiles(uint64_t n);
+// Histogram work of a sequence: tiles of the shared-bin kernel (small and
+// very large alphabets) and slabs of the packed kernel (the rest).
+uint32_t batch_hist_tiles(uint64_t n, uint64_t sigma);
+uint32_t batch_hist_slabs(uint64_t n, uint64_t sigma);
 cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32_t *hist_tile_start,
-                                 uint32_t hist_tiles, const uint32_t *lvl_start, uint32_t total_levels,
-                                 cudaStream_t st);
+                                 uint32_t hist_tiles, const uint32_t *slab_start, uint32_t slabs,
+                                 const uint32_t *lvl_start, uint32_t total_levels, cudaStream_t st);
 
 // Kernel (e): queries.
 cudaError_t launch_access(const TreeDesc *t, const uint64_t *i, uint64_t m, uint32_t *out, cudaStream_t st);

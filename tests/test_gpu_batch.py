@@ -90,3 +90,15 @@ def test_large_batch_of_small_sequences():
     trees = W.build_batch([to_dev(S) for S in seqs], [sp.sigma for sp in specs])
     for sp, S, t in zip(specs, seqs, trees):
         compare_tree(t, S, sp.sigma, check_dir=False)
+
+
+def test_batch_mid_alphabet_slabs():
+    """Sequences with 8K..96K codes take the packed histogram in 1M-symbol
+    slabs; a hot code passes the 2^15 hand-over inside one slab."""
+    W = wt()
+    seqs = [inputs.zipf((1 << 22) + 17, 65536, 1.3, 71, np.uint16), inputs.zipf(70_001, 20000, 1.1, 72, np.uint16),
+            inputs.uniform(5000, 256, 73, np.uint8), inputs.zipf(1 << 20, 65536, 1.0, 74, np.uint32)]
+    sigmas = [65536, 20000, 256, 65536]
+    trees = W.build_batch([to_dev(S) for S in seqs], sigmas)
+    for S, sigma, t in zip(seqs, sigmas, trees):
+        compare_tree(t, S, sigma, check_dir=len(S) < (1 << 21))

@@ -157,3 +157,20 @@ def test_many_tiles_per_cta_pipeline(sigma, dtype, log2n, alpha, variant):
     S = inputs.zipf(n, sigma, alpha, 4242, dtype) if alpha else inputs.uniform(n, sigma, 4242, dtype)
     t = W.Tree.build(to_dev(S), sigma, variant=variant)
     compare_tree(t, S, sigma)
+
+
+@pytest.mark.parametrize("sigma,dtype,n", [(65536, np.uint16, 1 << 25), (98304, np.uint32, 300_001),
+                                           (49153, np.uint16, 1_000_003)])
+def test_mid_alphabet_histogram(sigma, dtype, n):
+    """Alphabets of 48K..96K codes use packed 16-bit shared bins; a skewed
+    sequence drives its hottest bin past the 2^15 hand-over many times."""
+    W = wt()
+    S = inputs.zipf(n, sigma, 1.3, 901 + sigma, dtype)
+    t = W.Tree.build(to_dev(S), sigma, variant=W.VARIANT_LEVELWISE)
+    starts = W.node_starts(to_dev(S), sigma).cpu().numpy()
+    L = (sigma - 1).bit_length()
+    want = np.zeros((1 << L) + 1, np.uint64)
+    want[1:sigma + 1] = np.cumsum(np.bincount(S, minlength=sigma)).astype(np.uint64)
+    want[sigma + 1:] = n
+    assert np.array_equal(starts, want)
+    compare_tree(t, S, sigma, check_dir=n < (1 << 24))
