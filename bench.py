@@ -78,6 +78,43 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float, ws: int) -> float:
+    """The largest x over all ranks (x itself with one rank).  The tensor
+    lives where the process group's backend wants it (GPU for NCCL)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, ws: int) -> float:
+    """The sum of x over all ranks."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank does the same work)."""
+    return units_per_rank * ws / (ms * 1e-3)
+
+
+def barrier(ws: int) -> None:
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -261,16 +298,12 @@ def run_ours(args, ws, rank, local):
             t.free()
         return trees
 
-    def barrier():
-        if ws > 1:
-            dist.barrier()
-
     keep = []
     for _ in range(args.warmup):
         keep = step(keep)
     for t in keep:
         t.wait()
-    barrier()
+    barrier(ws)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -278,28 +311,23 @@ def run_ours(args, ws, rank, local):
     W.profile_begin()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
+    barrier(ws)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(args.steps):
         keep = step(keep)
     e1.record()
     torch.cuda.synchronize()
-    barrier()
+    barrier(ws)
     stats = W.profile_end()
     clk = clocks.stop()
     for t in keep:
         t.wait()
         t.free()
     keep = []
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, ws)
     syms_rank = sum(h.size for h in host)
-    syms = syms_rank * ws
-    value = syms / (ms * 1e-3)
+    value = job_rate(syms_rank, ws, ms)
 
     # End to end: the same step through the C ABI from pinned host buffers,
     # copies inside the timed region, query answers read back every step.
@@ -320,7 +348,7 @@ def run_ours(args, ws, rank, local):
     for _ in range(max(1, args.warmup // 2)):
         keep = step_e2e(keep)
     torch.cuda.synchronize()
-    barrier()
+    barrier(ws)
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record()
@@ -332,11 +360,7 @@ def run_ours(args, ws, rank, local):
     for t in keep:
         t.wait()
         t.free()
-    ms_e2e = f0.elapsed_time(f1) / e2e_steps
-    if ws > 1:
-        tt = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_e2e = float(tt.item())
+    ms_e2e = reduce_max(f0.elapsed_time(f1) / e2e_steps, ws)
     h2d = sum(h.nbytes for h in host) + sum(x.numel() * x.element_size() for x in q_p)
     d2h = QUERIES * 8
 
@@ -351,7 +375,7 @@ def run_ours(args, ws, rank, local):
                            variant={0: "auto", 1: "levelwise", 2: "dd"}[args.variant],
                            **({"reduced_size_log2": args.size_log2} if args.size_log2 else {})),
             "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": syms / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(syms_rank, ws, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
             "gpu_launches": launches, "clocks": clk, "kernels": kernels}
     print(json.dumps(line), flush=True)
@@ -447,18 +471,21 @@ def run_batch(args, ws, rank, local):
     W.profile_begin()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
     e0.record(st)
     for _ in range(args.steps):
         keep = step(keep)
     e1.record(st)
     torch.cuda.synchronize()
+    barrier(ws)
     stats = W.profile_end()
     clk = clocks.stop()
     for t in keep:
         t.wait()
         t.free()
-    ms = e0.elapsed_time(e1) / args.steps
-    value = n_total / (ms * 1e-3)
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, ws)
+    value = job_rate(n_total, ws, ms)
 
     # End to end: inputs copied from pinned host memory inside the timed region.
     stage = torch.empty(buf.numel(), dtype=torch.uint8).pin_memory()
@@ -478,7 +505,7 @@ def run_batch(args, ws, rank, local):
     for t in keep:
         t.wait()
         t.free()
-    ms_e2e = f0.elapsed_time(f1) / e2e_steps
+    ms_e2e = reduce_max(f0.elapsed_time(f1) / e2e_steps, ws)
     del buf, seqs, stage
 
     # Plain path per class: sigma x distribution, one 2^28-symbol sequence each.
@@ -518,7 +545,7 @@ def run_batch(args, ws, rank, local):
             "batch_efficiency_vs_plain": efficiency,
             "plain_rate_per_class": {f"sigma={k[0]} w={k[1]} {k[2]}": v for k, v in rate.items()},
             "roofline": roofline, "cpu_baseline": None,
-            "e2e": {"value": n_total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(n_total, ws, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 0, "ms_per_step": ms_e2e},
             "gpu_launches": launches, "clocks": clk, "kernels": kernels}
     print(json.dumps(line), flush=True)
@@ -608,7 +635,10 @@ def run_serve(args, ws, rank, local):
     meas = [r for r in srv.finished if r.rid >= warm]
     first = min(r.arrival for r in meas)
     last = max(r.done for r in meas)
-    value = sum(r.n for r in meas) / (last - first)
+    # replicas: every rank serves its own stream; the job's rate is all the
+    # symbols served over the slowest rank's span
+    span_s = reduce_max(last - first, ws)
+    value = reduce_sum(sum(r.n for r in meas), ws) / span_s
     build_lat = [(r.done - r.arrival) * 1e3 for r in meas]
     q_lat = [(q.done - q.issued) * 1e3 for q in qbs if getattr(q, "measured", False) and q.done]
     evicted = srv.evicted
