@@ -397,10 +397,10 @@ def roofline_of(stats: dict, steps: int):
                     "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(name),
                     "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
                     "avg_launch_ms": st["total_ms"] / st["launches"]}
-    kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / steps,
+    kernels = {k: {"launches": v["launches"], "cuda_kernels": v["kernels"], "ms_per_step": v["total_ms"] / steps,
                    "GBps": v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9 if v["total_ms"] > 0 else None}
                for k, v in stats.items()}
-    return roofline, kernels, sum(v["launches"] for v in stats.values())
+    return roofline, kernels, sum(v["kernels"] for v in stats.values())
 
 
 def _gen_parallel(specs):

@@ -248,13 +248,15 @@ wt_status wt_node_starts_noalloc(const void *S, uint64_t n, uint64_t sigma, int 
  * library is bracketed by CUDA events on the stream it runs on.
  * wt_profile_end waits for those events and writes one record per kernel
  * that ran (up to cap records to out; *count receives how many kernels
- * ran): launches, summed device time and summed algorithmic bytes (the
- * bytes the method must move for that launch: symbols read, bitmap and
- * directory written, next-level order written).
+ * ran): launches (timed calls), the CUDA kernels those calls launched,
+ * summed device time and summed algorithmic bytes (the bytes the method
+ * must move for that launch: symbols read, bitmap and directory written,
+ * next-level order written).
  */
 typedef struct {
     char name[24];
     uint64_t launches;
+    uint64_t kernels;
     double total_ms;
     double alg_bytes;
 } wt_kernel_stat_t;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <memory>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -76,7 +77,10 @@ struct ProfRecord {
     int kid;
     double bytes;
     cudaEvent_t e0, e1;
+    uint64_t k0, k1;  // kernel launch counter at the start and the end of the call
 };
+
+std::atomic<uint64_t> g_kernel_launches{0};
 
 struct Profiler {
     std::mutex mu;
@@ -108,7 +112,7 @@ struct ProfScope {
     ProfScope(int kid, double bytes, cudaStream_t s) : st(s) {
         std::lock_guard<std::mutex> lk(g_prof.mu);
         if (!g_prof.on) return;
-        ProfRecord r{kid, bytes, g_prof.take(), g_prof.take()};
+        ProfRecord r{kid, bytes, g_prof.take(), g_prof.take(), g_kernel_launches.load(), 0};
         if (!r.e0 || !r.e1) return;
         // Inside a stream capture the records become event nodes of the graph.
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -122,6 +126,7 @@ struct ProfScope {
         if (idx < 0) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
         cudaEventRecordWithFlags(g_prof.recs[idx].e1, st, flags);
+        g_prof.recs[idx].k1 = g_kernel_launches.load();
     }
 };
 
@@ -861,6 +866,8 @@ wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int 
 }  // namespace
 
 namespace wt {
+void note_launches(uint32_t k) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
+
 // Sets the calling thread's last status (for entry points in other files).
 wt_status record_status(wt_status s) { return set_last(s); }
 }  // namespace wt
@@ -1024,6 +1031,7 @@ wt_status wt_profile_end(wt_kernel_stat_t *out, uint32_t cap, uint32_t *count) {
             continue;
         }
         acc[rec.kid].launches++;
+        acc[rec.kid].kernels += rec.k1 - rec.k0;
         acc[rec.kid].total_ms += ms;
         acc[rec.kid].alg_bytes += rec.bytes;
         g_prof.pool.push_back(rec.e0);

@@ -194,7 +194,11 @@ cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32
                                  const uint32_t *lvl_start, uint32_t total_levels, cudaStream_t st) {
     if (nseq == 0) return cudaSuccess;
     batch_clear_err_kernel<<<(nseq + 255) / 256, 256, 0, st>>>(jobs, nseq);
-    if (hist_tiles) batch_hist_kernel<<<hist_tiles, kBatchThreads, 0, st>>>(jobs, hist_tile_start, nseq);
+    note_launches(1);
+    if (hist_tiles) {
+        batch_hist_kernel<<<hist_tiles, kBatchThreads, 0, st>>>(jobs, hist_tile_start, nseq);
+        note_launches(1);
+    }
     if (slabs) {
         const size_t smem = (kPackedMaxSigma / 2) * sizeof(uint32_t);
         static bool attr = false;
@@ -205,9 +209,14 @@ cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32
             attr = true;
         }
         batch_hist_packed_kernel<<<slabs, kPackedThreads, smem, st>>>(jobs, slab_start, nseq);
+        note_launches(1);
     }
     batch_starts_kernel<<<nseq, kBatchThreads, 0, st>>>(jobs);
-    if (total_levels) batch_tables_kernel<<<total_levels, kBatchThreads, 0, st>>>(jobs, lvl_start, nseq);
+    note_launches(1);
+    if (total_levels) {
+        batch_tables_kernel<<<total_levels, kBatchThreads, 0, st>>>(jobs, lvl_start, nseq);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 

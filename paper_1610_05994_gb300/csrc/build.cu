@@ -185,6 +185,7 @@ static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64
                                              (int)smem);
         if (e != cudaSuccess) return e;
         hist_shared_kernel<Sym><<<(unsigned)grid, kHistThreads, smem, st>>>(s, n, sig, copies, hist, err);
+        note_launches(1);
     } else if (sigma <= kPackedMaxSigma) {
         const size_t smem = (kPackedMaxSigma / 2) * sizeof(uint32_t);
         static bool attr = false;
@@ -198,8 +199,10 @@ static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64
         const uint64_t slab = ceil_div(n, g);
         hist_packed_kernel<Sym><<<(unsigned)ceil_div(n, slab), kPackedThreads, smem, st>>>(s, n, (uint32_t)sigma, slab,
                                                                                          hist, err);
+        note_launches(1);
     } else {
         hist_global_kernel<Sym><<<(unsigned)grid, kHistThreads, 0, st>>>(s, n, sigma, hist, err);
+        note_launches(1);
     }
     return cudaGetLastError();
 }
@@ -213,6 +216,7 @@ static cudaError_t histogram_rep_t(const void *S, uint64_t n, uint64_t sigma, ui
     if (grid > want) grid = want ? want : 1;
     hist_replicated_kernel<Sym><<<(unsigned)grid, kHistThreads, 0, st>>>(static_cast<const Sym *>(S), n, sigma, rep,
                                                                         R, err);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -356,8 +360,11 @@ template <class Val, class Out>
 static cudaError_t scan_large(Val val, Out out, uint64_t count, uint64_t *tmp, cudaStream_t st) {
     const uint64_t nchunks = ceil_div(count, kScanChunk);
     chunk_sums_kernel<Val><<<(unsigned)nchunks, kScanThreads, 0, st>>>(val, count, tmp);
+    note_launches(1);
     scan_sums_kernel<<<1, kScanThreads, 0, st>>>(tmp, nchunks);
+    note_launches(1);
     chunk_scan_kernel<Val, Out><<<(unsigned)nchunks, kScanThreads, 0, st>>>(val, out, count, tmp);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -386,6 +393,7 @@ cudaError_t launch_node_starts(const uint64_t *hist, uint64_t sigma, uint32_t L,
     const uint64_t entries = (1ull << L) + 1;
     if (tmp == nullptr || entries <= kSingleCtaMax) {
         node_starts_kernel<<<1, kScanThreads, 0, st>>>(hist, sigma, entries, hex);
+        note_launches(1);
         return cudaGetLastError();
     }
     return scan_large(HistVal{hist, sigma}, HexOut{hex}, entries, tmp, st);
@@ -430,6 +438,7 @@ cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, ui
     while (small < L && (1ull << small) <= kSingleCtaMax) small++;
     if (tmp == nullptr) small = L;
     node_tables_kernel<<<small, kScanThreads, 0, st>>>(hex, L, ob, ze);
+    note_launches(1);
     cudaError_t e = cudaGetLastError();
     for (uint32_t l = small; l < L && e == cudaSuccess; l++) {
         const uint64_t nodes = 1ull << l;

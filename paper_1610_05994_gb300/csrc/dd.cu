@@ -489,6 +489,7 @@ cudaError_t launch_dd_count(const void *S, uint64_t n, uint64_t sigma, const DdS
                             cudaStream_t st) {
     dd_count_kernel<<<(unsigned)dd_tiles(n), kDdThreads, 0, st>>>(static_cast<const uint8_t *>(S), n, (uint32_t)sigma,
                                                                   d.cnt, err);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -499,6 +500,7 @@ cudaError_t launch_dd_scan(uint64_t n, uint64_t sigma, const DdScratch &d, cudaS
     dd_colsum_kernel<<<(unsigned)chunks, 256, 0, st>>>(d.cnt, tiles, sig, d.csum);
     dd_chunkscan_kernel<<<1, 256, 0, st>>>(d.csum, chunks, sig, d.H);
     dd_offsets_kernel<<<(unsigned)chunks, 256, 0, st>>>(d.cnt, d.csum, tiles, sig, d.off);
+    note_launches(3);
     return cudaGetLastError();
 }
 
@@ -521,6 +523,7 @@ cudaError_t launch_dd_write(const void *S, uint64_t n, uint64_t sigma, uint32_t 
     a.err = err;
     dd_write_kernel<<<(unsigned)dd_tiles(n), kDdThreads, 0, st>>>(a);
     dd_finalize_kernel<<<1, 32, 0, st>>>(hex, L, a.nblocks, a.nspans, d_desc, a);
+    note_launches(2);
     return cudaGetLastError();
 }
 

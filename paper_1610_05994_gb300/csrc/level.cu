@@ -635,6 +635,7 @@ static cudaError_t launch_lw(const LevelLaunch &a, cudaStream_t st) {
     scan_segs_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
     const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
     level_pass_kernel<Sym><<<grid, kLwThreads, kLwSmem, st>>>(a);
+    note_launches(4);
     return cudaGetLastError();
 }
 
@@ -696,6 +697,7 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
     uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
     put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
+    note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, err, st);

@@ -204,6 +204,7 @@ static unsigned grid_for(uint64_t m) { return (unsigned)ceil_div(m, kQueryThread
 cudaError_t launch_access(const TreeDesc *t, const uint64_t *i, uint64_t m, uint32_t *out, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     access_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(t, i, m, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -211,6 +212,7 @@ cudaError_t launch_rank(const TreeDesc *t, const uint32_t *c, const uint64_t *i,
                         cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     rank_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(t, c, i, m, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -218,6 +220,7 @@ cudaError_t launch_select(const TreeDesc *t, const uint32_t *c, const uint64_t *
                           cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     select_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(t, c, j, m, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -226,6 +229,7 @@ cudaError_t launch_query_multi(const TreeDesc *const *trees, const uint32_t *tre
                                cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     multi_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(trees, tree_idx, op, c, arg, m, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 

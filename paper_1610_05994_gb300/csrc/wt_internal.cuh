@@ -175,6 +175,10 @@ __device__ __forceinline__ void packed_count(const Sym *__restrict__ S, uint64_t
 }
 
 // ------------------------------------------------------------ launchers
+// Every kernel launch of the library is counted (the profiler reports the
+// launches made inside each timed call).
+void note_launches(uint32_t k);
+
 // (defined in build.cu / query.cu, called from abi.cu)
 
 struct BuildScratch {

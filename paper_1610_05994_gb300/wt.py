@@ -45,7 +45,7 @@ class _Info(C.Structure):
 
 
 class _KernelStat(C.Structure):
-    _fields_ = [("name", C.c_char * 24), ("launches", C.c_uint64), ("total_ms", C.c_double),
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_uint64), ("kernels", C.c_uint64), ("total_ms", C.c_double),
                 ("alg_bytes", C.c_double)]
 
 
@@ -340,10 +340,11 @@ def profile_begin() -> None:
 
 
 def profile_end() -> dict:
-    """Stops timing; {kernel: {"launches", "total_ms", "alg_bytes"}}."""
+    """Stops timing; {kernel: {"launches", "kernels", "total_ms", "alg_bytes"}}."""
     cap = 32
     arr = (_KernelStat * cap)()
     cnt = C.c_uint32()
     _check(load().wt_profile_end(arr, cap, C.byref(cnt)), "wt_profile_end")
-    return {arr[k].name.decode(): {"launches": int(arr[k].launches), "total_ms": float(arr[k].total_ms),
-                                   "alg_bytes": float(arr[k].alg_bytes)} for k in range(min(cnt.value, cap))}
+    return {arr[k].name.decode(): {"launches": int(arr[k].launches), "kernels": int(arr[k].kernels),
+                                   "total_ms": float(arr[k].total_ms), "alg_bytes": float(arr[k].alg_bytes)}
+            for k in range(min(cnt.value, cap))}

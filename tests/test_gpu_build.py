@@ -41,7 +41,8 @@ def test_dd_rejects_what_it_cannot_build():
     assert e.value.status == W.ERR_ARG
 
 
-SIZES = [0, 1, 31, 32, 33, 511, 512, 513, 4095, 4096, 4097, 8193, 16383, 16384, 16385, 65535, 65537, 100003]
+SIZES = [0, 1, 31, 32, 33, 511, 512, 513, 2047, 2048, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 16383, 16384, 16385,
+         65535, 65537, 100003]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -58,7 +59,7 @@ def test_edge_shapes_u8(sigma, n, variant):
 
 @pytest.mark.parametrize("sigma,dtype", [(257, np.uint16), (1000, np.uint16), (65536, np.uint16),
                                          (4, np.uint32), (1 << 20, np.uint32), ((1 << 20) + 3, np.uint32)])
-@pytest.mark.parametrize("n", [1, 513, 4097, 70001])
+@pytest.mark.parametrize("n", [1, 513, 2047, 2048, 2049, 4096, 4097, 70001])
 def test_wide_symbols(sigma, dtype, n):
     W = wt()
     S = inputs.zipf(n, sigma, 1.2, 77 + n, dtype)
