@@ -474,13 +474,18 @@ void tree_destroy(wt_tree *t) {
 
 // ------------------------------------------------------------- batches
 
-// Pinned host staging for a batch's tables, reused across calls once the
-// copies of the previous call have completed.
-struct PinnedStaging {
-    std::mutex mu;
+// Pinned host staging for a batch's tables: two slots used in turn, so the
+// host prepares the next batch while the previous one still runs; a slot is
+// reused once the build that copied out of it has completed.
+struct PinnedSlot {
     void *ptr = nullptr;
     size_t bytes = 0;
-    cudaEvent_t ready = nullptr;  // the last copies out of the buffer
+    cudaEvent_t ready = nullptr;  // the end of the last build that used the slot
+};
+struct PinnedStaging {
+    std::mutex mu;
+    PinnedSlot slot[2];
+    uint32_t next = 0;
 };
 PinnedStaging g_pinned;
 
@@ -641,25 +646,26 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
 
     // Host tables, staged in pinned memory.
     std::lock_guard<std::mutex> lk(g_pinned.mu);
+    PinnedSlot &ps = g_pinned.slot[g_pinned.next++ & 1];
     const size_t stage_bytes = tbytes + desc_bytes;
-    if (g_pinned.ready && cudaEventSynchronize(g_pinned.ready) != cudaSuccess) cudaGetLastError();
-    if (g_pinned.bytes < stage_bytes) {
-        if (g_pinned.ptr) cudaFreeHost(g_pinned.ptr);
-        g_pinned.ptr = nullptr;
-        g_pinned.bytes = 0;
-        if (cudaMallocHost(&g_pinned.ptr, stage_bytes) != cudaSuccess) {
+    if (ps.ready && cudaEventSynchronize(ps.ready) != cudaSuccess) cudaGetLastError();
+    if (ps.bytes < stage_bytes) {
+        if (ps.ptr) cudaFreeHost(ps.ptr);
+        ps.ptr = nullptr;
+        ps.bytes = 0;
+        if (cudaMallocHost(&ps.ptr, stage_bytes) != cudaSuccess) {
             cudaGetLastError();
             dev_free(A, scratch, total_scratch, st);
             return WT_ERR_OOM;
         }
-        g_pinned.bytes = stage_bytes;
+        ps.bytes = stage_bytes;
     }
-    if (!g_pinned.ready && cudaEventCreateWithFlags(&g_pinned.ready, cudaEventDisableTiming) != cudaSuccess) {
+    if (!ps.ready && cudaEventCreateWithFlags(&ps.ready, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         dev_free(A, scratch, total_scratch, st);
         return WT_ERR_CUDA;
     }
-    char *ht = static_cast<char *>(g_pinned.ptr);
+    char *ht = static_cast<char *>(ps.ptr);
     SeqJob *hjobs = reinterpret_cast<SeqJob *>(ht + seqjob_off);
     uint32_t *hts = reinterpret_cast<uint32_t *>(ht + hts_off);
     uint32_t *lts = reinterpret_cast<uint32_t *>(ht + lts_off);
@@ -729,6 +735,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         ck(cudaMemsetAsync(B->d_err, 0, 4, st));
         ck(cudaMemcpyAsync(dt, ht, tbytes, cudaMemcpyHostToDevice, st));
         ck(cudaMemcpyAsync(d_descs, ht + tbytes, sizeof(TreeDesc) * count, cudaMemcpyHostToDevice, st));
+
         // empty sequences: R[0] = Hy[0] = 0
         for (uint32_t k = 0; k < count; k++)
             if (n[k] == 0)
@@ -771,7 +778,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
     }
-    ck(cudaEventRecord(g_pinned.ready, st));
+    ck(cudaEventRecord(ps.ready, st));
     ck(cudaEventRecord(B->done, st));
     dev_free(A, scratch, total_scratch, st);  // stream-ordered, after the batch
     if (r != WT_OK) {

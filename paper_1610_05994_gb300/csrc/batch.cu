@@ -72,15 +72,42 @@ __global__ void __launch_bounds__(kBatchThreads) batch_hist_kernel(const SeqJob 
         for (uint32_t c = threadIdx.x; c < sig * copies; c += blockDim.x) bins[c] = 0;
     __syncthreads();
     bool bad = false;
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-        const uint32_t s = load_sym(J.S, J.width, base + i);
+    auto add = [&](uint32_t s) {
         if ((uint64_t)s >= J.sigma)
             bad = true;
         else if (shared_bins)
             atomicAdd(&mine[s], 1u);
         else
             atomicAdd(reinterpret_cast<unsigned long long *>(&J.hist[s]), 1ull);
+    };
+    // Whole 16-byte vectors where the tile allows, single symbols elsewhere.
+    const unsigned char *tb = static_cast<const unsigned char *>(J.S) + base * J.width;
+    const uint32_t bytes = m * J.width;
+    const uint32_t head = (uint32_t)((16 - (reinterpret_cast<uintptr_t>(tb) & 15)) & 15) / J.width;
+    const uint32_t h = head < m ? head : m;
+    const uint32_t nvec = (bytes - h * J.width) / 16;
+    const uint4 *v = reinterpret_cast<const uint4 *>(tb + h * J.width);
+    for (uint32_t r = threadIdx.x; r < nvec; r += blockDim.x) {
+        const uint4 q = __ldcs(v + r);
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (J.width == 1) {
+                add(w4[k] & 0xffu);
+                add((w4[k] >> 8) & 0xffu);
+                add((w4[k] >> 16) & 0xffu);
+                add(w4[k] >> 24);
+            } else if (J.width == 2) {
+                add(w4[k] & 0xffffu);
+                add(w4[k] >> 16);
+            } else {
+                add(w4[k]);
+            }
+        }
     }
+    const uint32_t tail = h + nvec * 16 / J.width;
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x)
+        if (i < h || i >= tail) add(load_sym(J.S, J.width, base + i));
     if (bad) atomicOr(J.err, kErrSymbol);
     if (shared_bins) {
         __syncthreads();
@@ -105,11 +132,12 @@ __global__ void __launch_bounds__(kPackedThreads) batch_hist_packed_kernel(const
     __syncthreads();
     const uint64_t begin = (uint64_t)(blockIdx.x - slab_start[k]) * kBatchSlab;
     const uint64_t end = begin + kBatchSlab < J.n ? begin + kBatchSlab : J.n;
+    const bool sole = slab_start[k + 1] - slab_start[k] == 1;  // the sequence's only slab owns its histogram
     bool bad = false;
     if (J.width == 2)
-        packed_count<uint16_t>(static_cast<const uint16_t *>(J.S), begin, end, sigma, w, J.hist, bad);
+        packed_count<uint16_t>(static_cast<const uint16_t *>(J.S), begin, end, sigma, w, J.hist, bad, sole);
     else
-        packed_count<uint32_t>(static_cast<const uint32_t *>(J.S), begin, end, sigma, w, J.hist, bad);
+        packed_count<uint32_t>(static_cast<const uint32_t *>(J.S), begin, end, sigma, w, J.hist, bad, sole);
     if (bad) atomicOr(J.err, kErrSymbol);
 }
 
@@ -141,32 +169,70 @@ __device__ __forceinline__ uint64_t batch_block_scan(uint64_t v, uint64_t *s_war
     return r;
 }
 
+// Exclusive scan of `count` values (value(i) gives value i) into out(i, x),
+// by one CTA, in segments of kSeg values staged in shared memory so that
+// loads and stores are coalesced and each thread scans kPer consecutive
+// values.
+constexpr uint32_t kSegPer = 8;
+constexpr uint32_t kSeg = kBatchThreads * kSegPer;
+
+template <typename Val, typename Out>
+__device__ __forceinline__ void cta_scan(uint64_t count, Val value, Out out, uint64_t *seg, uint64_t *s_warp) {
+    uint64_t carry = 0;
+    for (uint64_t s0 = 0; s0 < count; s0 += kSeg) {
+#pragma unroll
+        for (uint32_t i = 0; i < kSegPer; i++) {
+            const uint64_t e = s0 + i * kBatchThreads + threadIdx.x;
+            seg[i * kBatchThreads + threadIdx.x] = e < count ? value(e) : 0;
+        }
+        __syncthreads();
+        uint64_t mine[kSegPer], sum = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kSegPer; i++) {
+            mine[i] = seg[threadIdx.x * kSegPer + i];
+            sum += mine[i];
+        }
+        uint64_t run = carry + batch_block_scan(sum, s_warp);
+#pragma unroll
+        for (uint32_t i = 0; i < kSegPer; i++) {
+            seg[threadIdx.x * kSegPer + i] = run;
+            run += mine[i];
+        }
+        if (threadIdx.x == kBatchThreads - 1) s_warp[32] = run;  // carry into the next segment
+        __syncthreads();
+#pragma unroll
+        for (uint32_t i = 0; i < kSegPer; i++) {
+            const uint64_t e = s0 + i * kBatchThreads + threadIdx.x;
+            if (e < count) out(e, seg[i * kBatchThreads + threadIdx.x]);
+        }
+        carry = s_warp[32];
+        __syncthreads();
+    }
+}
+
 // Node starts of every sequence: CTA k scans sequence k's histogram into Hex
 // (2^L + 1 entries, bins at and above sigma count 0).
 __global__ void __launch_bounds__(kBatchThreads) batch_starts_kernel(const SeqJob *__restrict__ jobs) {
-    __shared__ uint64_t s_warp[32];
+    __shared__ uint64_t s_warp[33];
+    __shared__ uint64_t seg[kSeg];
     const SeqJob &J = jobs[blockIdx.x];
     if (J.L == 0) return;
-    const uint64_t entries = (1ull << J.L) + 1;
-    const uint64_t chunk = ceil_div(entries, blockDim.x);
-    const uint64_t lo = threadIdx.x * chunk < entries ? threadIdx.x * chunk : entries;
-    const uint64_t hi = lo + chunk < entries ? lo + chunk : entries;
-    uint64_t sum = 0;
-    for (uint64_t c = lo; c < hi; c++) sum += c < J.sigma ? J.hist[c] : 0;
-    uint64_t run = batch_block_scan(sum, s_warp);
-    for (uint64_t c = lo; c < hi; c++) {
-        J.hex[c] = run;
-        run += c < J.sigma ? J.hist[c] : 0;
-    }
+    const uint64_t *hist = J.hist;
+    const uint64_t sigma = J.sigma;
+    uint64_t *hex = J.hex;
+    cta_scan((1ull << J.L) + 1, [&](uint64_t c) { return c < sigma ? hist[c] : 0ull; },
+             [&](uint64_t c, uint64_t v) { hex[c] = v; }, seg, s_warp);
 }
 
 // Node tables of every (sequence, level): CTA b takes one pair, found in the
 // prefix lvl_start of the sequences' level counts.  Same formulas as the
-// single-sequence node_tables_kernel.
+// single-sequence node_tables_kernel: the zeros of node v are the symbols of
+// its left child, OB = ones before the node's start, ZE = zeros up to its end.
 __global__ void __launch_bounds__(kBatchThreads) batch_tables_kernel(const SeqJob *__restrict__ jobs,
                                                                      const uint32_t *__restrict__ lvl_start,
                                                                      uint32_t nseq) {
-    __shared__ uint64_t s_warp[32];
+    __shared__ uint64_t s_warp[33];
+    __shared__ uint64_t seg[kSeg];
     const uint32_t k = find_seq(lvl_start, nseq, blockIdx.x);
     const SeqJob &J = jobs[k];
     const uint32_t l = blockIdx.x - lvl_start[k];
@@ -174,19 +240,14 @@ __global__ void __launch_bounds__(kBatchThreads) batch_tables_kernel(const SeqJo
     const uint64_t nodes = 1ull << l;
     const uint32_t sh = J.L - l;  // >= 1
     const uint64_t *hex = J.hex;
-    const uint64_t chunk = ceil_div(nodes, blockDim.x);
-    const uint64_t lo = threadIdx.x * chunk < nodes ? threadIdx.x * chunk : nodes;
-    const uint64_t hi = lo + chunk < nodes ? lo + chunk : nodes;
-    uint64_t sum = 0;
-    for (uint64_t v = lo; v < hi; v++) sum += hex[(2 * v + 1) << (sh - 1)] - hex[(2 * v) << (sh - 1)];
-    uint64_t zb = batch_block_scan(sum, s_warp);
     uint64_t *obl = J.ob + (nodes - 1), *zel = J.ze + (nodes - 1);
-    for (uint64_t v = lo; v < hi; v++) {
-        const uint64_t z = hex[(2 * v + 1) << (sh - 1)] - hex[(2 * v) << (sh - 1)];
-        obl[v] = hex[v << sh] - zb;
-        zel[v] = zb + z;
-        zb += z;
-    }
+    auto zeros = [&](uint64_t v) { return hex[(2 * v + 1) << (sh - 1)] - hex[(2 * v) << (sh - 1)]; };
+    cta_scan(nodes, zeros,
+             [&](uint64_t v, uint64_t zb) {
+                 obl[v] = hex[v << sh] - zb;
+                 zel[v] = zb + zeros(v);
+             },
+             seg, s_warp);
 }
 
 cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32_t *hist_tile_start,

@@ -152,23 +152,52 @@ __device__ __forceinline__ void packed_add(uint32_t *w, uint64_t *hist, uint32_t
 
 // Counts S[begin, end) (all threads of the CTA) into the shared words w
 // (zeroed), then adds them to hist and clears w again.  Returns (in bad)
-// whether a symbol was >= sigma.
+// whether a symbol was >= sigma.  sole: this CTA is the only one counting
+// into hist (which is zero), so the counts are stored, not added; hand-overs
+// of 2^15 still add, before the barrier that precedes the stores.
 template <typename Sym>
 __device__ __forceinline__ void packed_count(const Sym *__restrict__ S, uint64_t begin, uint64_t end, uint32_t sigma,
-                                             uint32_t *w, uint64_t *hist, bool &bad) {
-    for (uint64_t k = begin + threadIdx.x; k < end; k += blockDim.x) {
-        const uint32_t s = (uint32_t)S[k];
+                                             uint32_t *w, uint64_t *hist, bool &bad, bool sole = false) {
+    auto add = [&](uint32_t s) {
         if (s < sigma)
             packed_add(w, hist, s);
         else
             bad = true;
+    };
+    constexpr uint32_t kPer = 16 / sizeof(Sym);
+    const uint64_t vbegin = (begin + kPer - 1) / kPer * kPer, vend = end / kPer * kPer;
+    if ((reinterpret_cast<uintptr_t>(S) & 15) == 0 && vbegin < vend) {
+        const uint4 *V = reinterpret_cast<const uint4 *>(S);
+        for (uint64_t r = vbegin / kPer + threadIdx.x; r < vend / kPer; r += blockDim.x) {
+            const uint4 q = __ldcs(V + r);
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (sizeof(Sym) == 2) {
+                    add(w4[k] & 0xffffu);
+                    add(w4[k] >> 16);
+                } else {
+                    add(w4[k]);
+                }
+            }
+        }
+        for (uint64_t k = begin + threadIdx.x; k < vbegin; k += blockDim.x) add((uint32_t)S[k]);
+        for (uint64_t k = vend + threadIdx.x; k < end; k += blockDim.x) add((uint32_t)S[k]);
+    } else {
+        for (uint64_t k = begin + threadIdx.x; k < end; k += blockDim.x) add((uint32_t)S[k]);
     }
     __syncthreads();
     const uint32_t words = (sigma + 1) / 2;
     for (uint32_t j = threadIdx.x; j < words; j += blockDim.x) {
         const uint32_t v = w[j];
-        if (v & 0xffffu) atomicAdd(reinterpret_cast<unsigned long long *>(&hist[2 * j]), (unsigned long long)(v & 0xffffu));
-        if (v >> 16) atomicAdd(reinterpret_cast<unsigned long long *>(&hist[2 * j + 1]), (unsigned long long)(v >> 16));
+        if (sole) {
+            if (v & 0xffffu) hist[2 * j] += v & 0xffffu;
+            if (v >> 16) hist[2 * j + 1] += v >> 16;
+        } else {
+            if (v & 0xffffu)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&hist[2 * j]), (unsigned long long)(v & 0xffffu));
+            if (v >> 16) atomicAdd(reinterpret_cast<unsigned long long *>(&hist[2 * j + 1]), (unsigned long long)(v >> 16));
+        }
         w[j] = 0;
     }
     __syncthreads();
