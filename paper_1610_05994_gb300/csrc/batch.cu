@@ -38,84 +38,120 @@ __device__ __forceinline__ uint32_t find_seq(const uint32_t *start, uint32_t cou
     return lo;
 }
 
-__device__ __forceinline__ uint32_t load_sym(const void *S, int width, uint64_t j) {
-    if (width == 1) return static_cast<const uint8_t *>(S)[j];
-    if (width == 2) return static_cast<const uint16_t *>(S)[j];
-    return static_cast<const uint32_t *>(S)[j];
-}
-
 // Zeroes every sequence's error word (they live in the trees' memory).
 __global__ void batch_clear_err_kernel(const SeqJob *__restrict__ jobs, uint32_t nseq) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < nseq) *jobs[k].err = 0;
 }
 
-// Leaf histogram of the sequences with small (or very large) alphabets:
-// CTA b takes one tile of one sequence.
+// One symbol into the bins: the CTA's shared bins (`mine`: this warp's
+// copy), or, for alphabets above the shared bins, a 64-bit atomic on the
+// sequence's histogram.
+__device__ __forceinline__ void batch_add(uint32_t s, uint64_t sigma, uint32_t *mine, uint64_t *hist,
+                                          bool shared_bins, bool &bad) {
+    if ((uint64_t)s >= sigma)
+        bad = true;
+    else if (shared_bins)
+        atomicAdd(&mine[s], 1u);
+    else
+        atomicAdd(reinterpret_cast<unsigned long long *>(&hist[s]), 1ull);
+}
+
+template <typename Sym>
+__device__ __forceinline__ void batch_add_vec(const uint4 q, uint64_t sigma, uint32_t *mine, uint64_t *hist,
+                                              bool shared_bins, bool &bad) {
+    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (sizeof(Sym) == 1) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) batch_add((w4[k] >> (8 * j)) & 0xffu, sigma, mine, hist, shared_bins, bad);
+        } else if (sizeof(Sym) == 2) {
+            batch_add(w4[k] & 0xffffu, sigma, mine, hist, shared_bins, bad);
+            batch_add(w4[k] >> 16, sigma, mine, hist, shared_bins, bad);
+        } else {
+            batch_add(w4[k], sigma, mine, hist, shared_bins, bad);
+        }
+    }
+}
+
+// Symbols [b, e) of one sequence into the bins: whole 16-byte vectors, four
+// in flight per thread, single symbols at the ends.
+template <typename Sym>
+__device__ __forceinline__ void batch_count_range(const SeqJob &J, uint64_t b, uint64_t e, uint32_t *mine,
+                                                  bool shared_bins, bool &bad) {
+    constexpr uint32_t kPer = 16 / sizeof(Sym);
+    const Sym *S = static_cast<const Sym *>(J.S);
+    const uint64_t sigma = J.sigma;
+    uint64_t *hist = J.hist;
+    const uint64_t head = ((16 - (reinterpret_cast<uintptr_t>(S + b) & 15)) & 15) / sizeof(Sym);
+    const uint64_t a = b + head < e ? b + head : e;
+    const uint64_t nvec = (e - a) / kPer;
+    const uint4 *V = reinterpret_cast<const uint4 *>(S + a);
+    const uint32_t T = blockDim.x;
+    uint64_t r = threadIdx.x;
+    for (; r + 3 * T < nvec; r += 4 * T) {
+        const uint4 q0 = __ldcs(V + r), q1 = __ldcs(V + r + T), q2 = __ldcs(V + r + 2 * T), q3 = __ldcs(V + r + 3 * T);
+        batch_add_vec<Sym>(q0, sigma, mine, hist, shared_bins, bad);
+        batch_add_vec<Sym>(q1, sigma, mine, hist, shared_bins, bad);
+        batch_add_vec<Sym>(q2, sigma, mine, hist, shared_bins, bad);
+        batch_add_vec<Sym>(q3, sigma, mine, hist, shared_bins, bad);
+    }
+    for (; r < nvec; r += T) batch_add_vec<Sym>(__ldcs(V + r), sigma, mine, hist, shared_bins, bad);
+    for (uint64_t i = b + threadIdx.x; i < a; i += T) batch_add((uint32_t)S[i], sigma, mine, hist, shared_bins, bad);
+    for (uint64_t i = a + nvec * kPer + threadIdx.x; i < e; i += T)
+        batch_add((uint32_t)S[i], sigma, mine, hist, shared_bins, bad);
+}
+
+// Leaf histogram of the sequences with small (or very large) alphabets.
+// Persistent: CTA b takes a contiguous range of the launch's tiles
+// (tile_start: each sequence's first tile, total at [nseq]), so it finds its
+// first sequence once, walks forward, and zeroes and flushes its shared bins
+// once per sequence of its range.
 __global__ void __launch_bounds__(kBatchThreads) batch_hist_kernel(const SeqJob *__restrict__ jobs,
                                                                    const uint32_t *__restrict__ tile_start,
                                                                    uint32_t nseq) {
     __shared__ uint32_t bins[kBatchSmemBins];
-    const uint32_t k = find_seq(tile_start, nseq, blockIdx.x);
-    const SeqJob &J = jobs[k];
-    const uint64_t base = (uint64_t)(blockIdx.x - tile_start[k]) * kBatchHistTile;
-    if (base >= J.n) return;
-    const uint32_t m = (uint32_t)((J.n - base) < kBatchHistTile ? (J.n - base) : kBatchHistTile);
-    const bool shared_bins = J.sigma <= kBatchSmemBins;
-    // Small alphabets: one private copy of the bins per warp (up to all
-    // warps), so the warps of a CTA do not queue on the same few words.
-    const uint32_t sig = (uint32_t)J.sigma;
-    uint32_t copies = shared_bins ? kBatchSmemBins / sig : 1;
-    if (copies > kBatchThreads / 32) copies = kBatchThreads / 32;
-    uint32_t *mine = bins + ((threadIdx.x >> 5) % copies) * sig;
-    if (shared_bins)
-        for (uint32_t c = threadIdx.x; c < sig * copies; c += blockDim.x) bins[c] = 0;
-    __syncthreads();
-    bool bad = false;
-    auto add = [&](uint32_t s) {
-        if ((uint64_t)s >= J.sigma)
-            bad = true;
-        else if (shared_bins)
-            atomicAdd(&mine[s], 1u);
-        else
-            atomicAdd(reinterpret_cast<unsigned long long *>(&J.hist[s]), 1ull);
-    };
-    // Whole 16-byte vectors where the tile allows, single symbols elsewhere.
-    const unsigned char *tb = static_cast<const unsigned char *>(J.S) + base * J.width;
-    const uint32_t bytes = m * J.width;
-    const uint32_t head = (uint32_t)((16 - (reinterpret_cast<uintptr_t>(tb) & 15)) & 15) / J.width;
-    const uint32_t h = head < m ? head : m;
-    const uint32_t nvec = (bytes - h * J.width) / 16;
-    const uint4 *v = reinterpret_cast<const uint4 *>(tb + h * J.width);
-    for (uint32_t r = threadIdx.x; r < nvec; r += blockDim.x) {
-        const uint4 q = __ldcs(v + r);
-        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (J.width == 1) {
-                add(w4[k] & 0xffu);
-                add((w4[k] >> 8) & 0xffu);
-                add((w4[k] >> 16) & 0xffu);
-                add(w4[k] >> 24);
-            } else if (J.width == 2) {
-                add(w4[k] & 0xffffu);
-                add(w4[k] >> 16);
-            } else {
-                add(w4[k]);
-            }
-        }
-    }
-    const uint32_t tail = h + nvec * 16 / J.width;
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x)
-        if (i < h || i >= tail) add(load_sym(J.S, J.width, base + i));
-    if (bad) atomicOr(J.err, kErrSymbol);
-    if (shared_bins) {
+    const uint32_t total = tile_start[nseq];
+    const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
+    uint32_t t0 = min(blockIdx.x * per, total);
+    const uint32_t t1 = min(t0 + per, total);
+    if (t0 >= t1) return;
+    uint32_t k = find_seq(tile_start, nseq, t0);
+    while (t0 < t1) {
+        const SeqJob &J = jobs[k];
+        const uint32_t ks = tile_start[k];
+        const uint32_t te = min(t1, tile_start[k + 1]);
+        const uint64_t b = (uint64_t)(t0 - ks) * kBatchHistTile;
+        const uint64_t e = min(J.n, (uint64_t)(te - ks) * kBatchHistTile);
+        const bool shared_bins = J.sigma <= kBatchSmemBins;
+        // Small alphabets: one private copy of the bins per warp (up to all
+        // warps), so the warps of a CTA do not queue on the same few words.
+        const uint32_t sig = (uint32_t)J.sigma;
+        uint32_t copies = shared_bins ? kBatchSmemBins / sig : 1;
+        if (copies > kBatchThreads / 32) copies = kBatchThreads / 32;
+        uint32_t *mine = bins + ((threadIdx.x >> 5) % copies) * sig;
+        if (shared_bins)
+            for (uint32_t c = threadIdx.x; c < sig * copies; c += blockDim.x) bins[c] = 0;
         __syncthreads();
-        for (uint32_t c = threadIdx.x; c < sig; c += blockDim.x) {
-            uint32_t sum = 0;
-            for (uint32_t q = 0; q < copies; q++) sum += bins[q * sig + c];
-            if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&J.hist[c]), (unsigned long long)sum);
-        }
+        bool bad = false;
+        if (J.width == 1)
+            batch_count_range<uint8_t>(J, b, e, mine, shared_bins, bad);
+        else if (J.width == 2)
+            batch_count_range<uint16_t>(J, b, e, mine, shared_bins, bad);
+        else
+            batch_count_range<uint32_t>(J, b, e, mine, shared_bins, bad);
+        if (bad) atomicOr(J.err, kErrSymbol);
+        __syncthreads();
+        if (shared_bins)
+            for (uint32_t c = threadIdx.x; c < sig; c += blockDim.x) {
+                uint32_t sum = 0;
+                for (uint32_t q = 0; q < copies; q++) sum += bins[q * sig + c];
+                if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&J.hist[c]), (unsigned long long)sum);
+            }
+        __syncthreads();  // the bins are zeroed again for the next sequence
+        t0 = te;
+        while (k + 1 < nseq && tile_start[k + 1] <= t0) k++;
     }
 }
 
@@ -257,7 +293,22 @@ cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32
     batch_clear_err_kernel<<<(nseq + 255) / 256, 256, 0, st>>>(jobs, nseq);
     note_launches(1);
     if (hist_tiles) {
-        batch_hist_kernel<<<hist_tiles, kBatchThreads, 0, st>>>(jobs, hist_tile_start, nseq);
+        // Persistent: every resident CTA slot.
+        static uint32_t slots = 0;
+        if (!slots) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_hist_kernel, kBatchThreads, 0) !=
+                    cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+            slots = (uint32_t)(sms > 0 ? sms : 1) * (uint32_t)per_sm;
+        }
+        batch_hist_kernel<<<hist_tiles < slots ? hist_tiles : slots, kBatchThreads, 0, st>>>(jobs, hist_tile_start,
+                                                                                             nseq);
         note_launches(1);
     }
     if (slabs) {

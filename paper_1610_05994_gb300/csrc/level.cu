@@ -168,42 +168,57 @@ __device__ __forceinline__ void store_run(uintptr_t g0, uint32_t len, const unsi
 // ---------------------------------------------------------------- counts
 
 // The level-l ones of every tile of P_l: symbols with bit L - 1 - l set.
+// One warp per tile, the warps of the grid striding over the tiles together
+// (a window of consecutive tiles in flight, eight 16-byte loads per lane);
+// each warp finds a tile's job by binary search from its previous one.
+constexpr int kCountThreads = 256;
+constexpr int kCountWarps = kCountThreads / 32;
+
 template <typename Sym>
-__global__ void __launch_bounds__(256) count_kernel(LevelLaunch a) {
+__global__ void __launch_bounds__(kCountThreads) count_kernel(LevelLaunch a) {
     using Cfg = LwCfg<Sym>;
-    __shared__ uint32_t part[8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t k = blockIdx.x < a.total_tiles ? find_job(a, blockIdx.x) : 0;
-    for (uint32_t g = blockIdx.x; g < a.total_tiles; g += gridDim.x) {
-        while (k + 1 < a.njobs && a.tile_start[k + 1] <= g) k++;
+    constexpr int kVecs = (int)(kLwTileBytes / 512);  // 16-byte loads per lane per tile
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * kCountWarps;
+    const uint32_t bsh_l = 1 + a.l;
+    uint32_t k = 0;
+    for (uint32_t g = blockIdx.x * kCountWarps + (threadIdx.x >> 5); g < a.total_tiles; g += nwarps) {
+        if (k + 1 < a.njobs && a.tile_start[k + 1] <= g) {
+            uint32_t lo = k + 1, hi = a.njobs - 1;  // the last job starting at or before g
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (a.tile_start[mid] <= g)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            k = lo;
+        }
         const LevelJob &J = a.jobs[k];
         const Sym *S = static_cast<const Sym *>(J.cur);
         const uint32_t tile = g - a.tile_start[k];
         const uint64_t base = (uint64_t)tile * Cfg::kTile;
         const uint32_t cnt = (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
-        const uint32_t bsh = J.L - 1 - a.l;
+        const uint32_t bsh = J.L - bsh_l;
         uint32_t c = 0;
         if (cnt == Cfg::kTile && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
-            const uint4 *v = reinterpret_cast<const uint4 *>(S + base);
+            const uint4 *v = reinterpret_cast<const uint4 *>(S + base) + lane;
 #pragma unroll
-            for (int r = 0; r < (int)(kLwTileBytes / 16 / 256); r++) {
-                const uint4 w = __ldcs(v + r * 256 + tid);
-                const uint32_t x[4] = {w.x, w.y, w.z, w.w};
-                c += __popc(chunk_bits<Sym>(x, bsh));
+            for (int h = 0; h < kVecs; h += 8) {
+                uint4 w[8];
+#pragma unroll
+                for (int r = 0; r < 8; r++) w[r] = __ldcs(v + (h + r) * 32);
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
+                    c += __popc(chunk_bits<Sym>(x, bsh));
+                }
             }
         } else {
-            for (uint32_t p = tid; p < cnt; p += 256) c += ((uint32_t)S[base + p] >> bsh) & 1u;
+            for (uint32_t p = lane; p < cnt; p += 32) c += ((uint32_t)S[base + p] >> bsh) & 1u;
         }
         c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0) part[warp] = c;
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t t = 0;
-#pragma unroll
-            for (int w = 0; w < 8; w++) t += part[w];
-            J.cnt[tile] = t;
-        }
-        __syncthreads();
+        if (lane == 0) J.cnt[tile] = c;
     }
 }
 
@@ -500,29 +515,34 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                 }
             }
         } else {
-            uint32_t stx = 0;
-#pragma unroll
-            for (int st = 0; st < kLwSteps; st++) {
-                const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;
-                uint32_t o = wx + stx + ((lpk >> (16 * st)) & 0xffffu);
-                stx += (tpk >> (16 * st)) & 0xffffu;
-#pragma unroll
-                for (int kk = 0; kk < kSps; kk++) {
-                    const uint32_t p = q / kW + kk;  // tile position
-                    if (!kWhole && p >= cnt) continue;
-                    const uint32_t sv = sym_at<Sym>(x[st], kk);
-                    const uint32_t bit = (h[st] >> kk) & 1u;
+            // Several nodes: each symbol to its own position (Proposition 1).
+            // A warp takes 32 consecutive symbols of its range per round, so
+            // one store instruction covers runs of consecutive destinations
+            // and the node tables are read once per node; the ones before a
+            // symbol come from a ballot over the round.
+            constexpr uint32_t kWarpSyms = kLwWarpBytes / kW;
+            const uint32_t lt = (1u << lane) - 1u;
+            uint32_t o = wx;  // ones of the tile before this round
+#pragma unroll 4
+            for (uint32_t g = 0; g < kWarpSyms; g += 32) {
+                const uint32_t p = warp * kWarpSyms + g + lane;  // tile position
+                const bool in = kWhole || p < cnt;
+                const uint32_t sv = in ? (uint32_t)sb[p] : 0u;
+                const uint32_t bit = (sv >> bsh) & 1u;
+                const uint32_t bal = __ballot_sync(0xffffffffu, in && bit);
+                const uint32_t ob = o + __popc(bal & lt);  // ones of the tile before p
+                o += __popc(bal);
+                if (in) {
                     const uint32_t v = sv >> shv;
                     if (v >= nodes) {
                         bad = true;
-                        continue;
+                    } else {
+                        const uint64_t dst = bit ? P + ob + __ldg(J.ze + v) : (base + p - P - ob) + __ldg(J.ob + v);
+                        if (dst < J.n)
+                            nxt[dst] = (Sym)sv;
+                        else
+                            bad = true;
                     }
-                    const uint64_t dst = bit ? P + o + __ldg(J.ze + v) : (base + p - P - o) + __ldg(J.ob + v);
-                    if (dst < J.n)
-                        nxt[dst] = (Sym)sv;
-                    else
-                        bad = true;
-                    o += bit;
                 }
             }
         }
@@ -629,8 +649,10 @@ static cudaError_t launch_lw(const LevelLaunch &a, cudaStream_t st) {
         }
         slots = sms * per_sm;
     }
-    const uint32_t g0 = a.total_tiles < (uint32_t)(sms * 8) ? a.total_tiles : (uint32_t)(sms * 8);
-    count_kernel<Sym><<<g0, 256, 0, st>>>(a);
+    // Counts: a warp per tile, at most eight CTAs per SM.
+    const uint32_t cw = (a.total_tiles + kCountWarps - 1) / kCountWarps;
+    const uint32_t g0 = cw < (uint32_t)(sms * 8) ? cw : (uint32_t)(sms * 8);
+    count_kernel<Sym><<<g0, kCountThreads, 0, st>>>(a);
     scan_sums_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
     scan_segs_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
     const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
