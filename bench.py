@@ -21,6 +21,11 @@ requests at 70% of the measured batched build throughput, continuous
 batching under a 120 GB budget, batches of 2^16 mixed queries against the
 resident trees, and reports p50/p99 build and query latency.
 
+``--workload locality`` builds the paper's locality stress inputs (Section 4,
+cont and rand): n = 2^30 four-byte codes over sigma = 2^y, y in {4, 6, ...,
+14}, each code n / sigma times, in code order (cont) or at random positions
+(rand); one line with the whole set's throughput and each input's rate.
+
 ``--impl reference`` times the CPU oracle instead (single thread, bounded
 sample of the same workload).  Under torchrun every rank builds its own
 replica (weak scaling, no collective on the data path); rank 0 prints.
@@ -381,6 +386,88 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+LOCALITY_N = 1 << 30
+
+
+def run_locality(args, ws, rank, local):
+    """Builds of the cont and rand inputs for every sigma = 2^y: per input W
+    untimed and K timed builds (CUDA events), the whole set's symbols over
+    the sum of the per-input times, and each input's own rate."""
+    import torch
+
+    from paper_1610_05994_gb300 import build as B
+    from paper_1610_05994_gb300 import wt as W
+
+    torch.cuda.set_device(local)
+    B.build_library()
+    W.load()
+    dev = torch.device("cuda", local)
+    n = LOCALITY_N if not args.size_log2 else min(LOCALITY_N, 1 << args.size_log2)
+    per, stats, total_ms, e2e = [], {}, 0.0, None
+    clocks = ClockSampler(local)
+    clocks.start()
+    for y in inputs.LOCALITY_SIZES:
+        for kind in ("cont", "rand"):
+            sigma = 1 << y
+            S = inputs.locality_torch(n, sigma, kind, inputs.SEED_BASE + 100 + y, dev)
+            for _ in range(args.warmup):
+                W.Tree.build(S, sigma, wait=False).free()
+            torch.cuda.synchronize()
+            barrier(ws)
+            W.profile_begin()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                W.Tree.build(S, sigma, wait=False).free()
+            e1.record()
+            torch.cuda.synchronize()
+            st = W.profile_end()
+            ms = reduce_max(e0.elapsed_time(e1) / args.steps, ws)
+            for k, v in st.items():
+                acc = stats.setdefault(k, {"launches": 0, "kernels": 0, "total_ms": 0.0, "alg_bytes": 0.0})
+                for f in acc:
+                    acc[f] += v[f]
+            lp = st.get("level_pass")
+            per.append({"sigma": sigma, "kind": kind, "ms_per_build": ms, "symbols_per_s": n / (ms * 1e-3),
+                        "level_pass_GBps": lp["alg_bytes"] / lp["total_ms"] / 1e6 if lp else None})
+            total_ms += ms
+            if y == inputs.LOCALITY_SIZES[-1] and kind == "rand":
+                # End to end for this input: the build from a pinned host copy.
+                host = S.cpu().pin_memory()
+                _build_from_host(W, host, sigma, 0).free()
+                torch.cuda.synchronize()
+                f0 = torch.cuda.Event(enable_timing=True)
+                f1 = torch.cuda.Event(enable_timing=True)
+                k2 = max(1, min(args.steps, 3))
+                f0.record()
+                for _ in range(k2):
+                    _build_from_host(W, host, sigma, 0).free()
+                f1.record()
+                torch.cuda.synchronize()
+                e2e = {"ms": reduce_max(f0.elapsed_time(f1) / k2, ws), "bytes": host.numel() * host.element_size()}
+                del host
+            del S
+            torch.cuda.empty_cache()
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    roofline, kernels, launches = roofline_of(stats, args.steps)
+    line = {"metric": METRIC, "value": job_rate(n * len(per), ws, total_ms), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"locality stress (cont and rand): n={n} u32 codes, sigma=2^y for y in "
+                                   f"{list(inputs.LOCALITY_SIZES)}; a step builds each of the {len(per)} inputs once",
+                       "parallelism": f"replicas{ws}", "l2": "inputs (4 GiB each) larger than L2; no flush",
+                       "inputs": per},
+            "roofline": roofline, "cpu_baseline": None,
+            "e2e": ({"value": job_rate(n, ws, e2e["ms"]), "unit": UNIT, "h2d_bytes_per_step": e2e["bytes"],
+                     "d2h_bytes_per_step": 0, "input": f"rand, sigma=2^{inputs.LOCALITY_SIZES[-1]}"}
+                    if e2e else None),
+            "gpu_launches": launches, "clocks": clk, "kernels": kernels}
+    print(json.dumps(line), flush=True)
+
+
 def roofline_of(stats: dict, steps: int):
     """Roofline of the kernel with the largest device time, per-kernel
     figures per step, and the number of library launches, from the library's
@@ -708,7 +795,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + ["batch", "serve"], default="text+dna")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + ["batch", "serve", "locality"],
+                    default="text+dna")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured build requests")
     ap.add_argument("--size-log2", type=int, default=0,
                     help="profiling aid: cap each sequence at 2^k symbols (the line then names the cap)")
@@ -717,7 +805,7 @@ def main():
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
-        if args.workload in ("batch", "serve"):
+        if args.workload in ("batch", "serve", "locality"):
             print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed on the single-sequence "
                               "workloads only"}), flush=True)
             return
@@ -727,7 +815,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        {"batch": run_batch, "serve": run_serve}.get(args.workload, run_ours)(args, ws, rank, local)
+        {"batch": run_batch, "serve": run_serve, "locality": run_locality}.get(args.workload, run_ours)(
+            args, ws, rank, local)
     finally:
         if ws > 1:
             import torch.distributed as dist

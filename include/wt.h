@@ -100,14 +100,14 @@ wt_status wt_wait(wt_handle h);
 
 /*
  * Builds count trees in one batch (the sequences may differ in n, sigma and
- * width): one launch computes every sequence's histogram, one its node
- * starts, one its node tables, then one launch per (symbol width, level)
+ * width): one launch computes every sequence's histogram, a few launches
+ * its node starts and node tables, then one launch per (symbol width, level)
  * runs the level pass of Algorithm 1's levels over every sequence that has
  * that level.  On a non-default stream the launches are captured into one
  * CUDA graph and launched together.  The trees share one device block,
  * released when the last of them is freed.  S[k] are device pointers
- * (n[k] < 2^40).  Any argument error builds nothing: every out[k] is NULL
- * and the error is returned.  Asynchronous on stream; wt_wait on a handle
+ * (n[k] < 2^40); count < 2^27.  Any argument error builds nothing: every
+ * out[k] is NULL and the error is returned.  Asynchronous on stream; wt_wait on a handle
  * returns that sequence's status (a device-side give-up anywhere in the
  * batch is reported by every handle).
  */

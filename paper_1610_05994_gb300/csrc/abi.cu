@@ -521,6 +521,7 @@ void carve_levels(TreeDesc &d, char *p, uint64_t n, uint32_t L) {
 wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64_t *sigma, const int *width,
                            uint32_t count, wt_handle *out, cudaStream_t st) {
     for (uint32_t k = 0; k < count; k++) out[k] = nullptr;
+    if (count >= (1u << 27)) return WT_ERR_ARG;  // (sequence, level) pairs are packed as k << 5 | l
     for (uint32_t k = 0; k < count; k++) {
         wt_status r = check_args(S[k], n[k], sigma[k], width[k]);
         if (r != WT_OK) return r;
@@ -630,8 +631,24 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
     tbytes += align256(4 * ((size_t)count + 1));
     const size_t sls_off = tbytes;
     tbytes += align256(4 * ((size_t)count + 1));
-    const size_t lts_off = tbytes;
-    tbytes += align256(4 * ((size_t)count + 1));
+    uint32_t nsmall = 0, nbig = 0, nbig_pairs = 0, nsmall_pairs = 0;
+    for (uint32_t k = 0; k < count; k++) {
+        if (L[k] == 0) continue;
+        if (batch_small_alphabet(L[k])) {
+            nsmall++;
+        } else {
+            nbig++;
+            for (uint32_t l = 0; l < L[k]; l++) ((1ull << l) > kBatchWarpLeaves ? nbig_pairs : nsmall_pairs)++;
+        }
+    }
+    const size_t small_off = tbytes;
+    tbytes += align256(4 * ((size_t)nsmall + 1));
+    const size_t big_off = tbytes;
+    tbytes += align256(4 * ((size_t)nbig + 1));
+    const size_t bpairs_off = tbytes;
+    tbytes += align256(4 * ((size_t)nbig_pairs + 1));
+    const size_t spairs_off = tbytes;
+    tbytes += align256(4 * ((size_t)nsmall_pairs + 1));
     for (auto &P : plans) {
         P.jobs_off = tbytes;
         tbytes += align256(sizeof(LevelJob) * P.seqs.size());
@@ -668,9 +685,12 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
     char *ht = static_cast<char *>(ps.ptr);
     SeqJob *hjobs = reinterpret_cast<SeqJob *>(ht + seqjob_off);
     uint32_t *hts = reinterpret_cast<uint32_t *>(ht + hts_off);
-    uint32_t *lts = reinterpret_cast<uint32_t *>(ht + lts_off);
     uint32_t *sls = reinterpret_cast<uint32_t *>(ht + sls_off);
-    uint32_t hist_tiles = 0, hist_slabs = 0, total_levels = 0;
+    uint32_t *hsmall = reinterpret_cast<uint32_t *>(ht + small_off);
+    uint32_t *hbig = reinterpret_cast<uint32_t *>(ht + big_off);
+    uint32_t *hbpairs = reinterpret_cast<uint32_t *>(ht + bpairs_off);
+    uint32_t *hspairs = reinterpret_cast<uint32_t *>(ht + spairs_off);
+    uint32_t hist_tiles = 0, hist_slabs = 0, ismall = 0, ibig = 0, ibpair = 0, ispair = 0;
     for (uint32_t k = 0; k < count; k++) {
         SeqJob &J = hjobs[k];
         J.S = S[k];
@@ -687,12 +707,22 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         hist_tiles += batch_hist_tiles(n[k], sigma[k]);
         sls[k] = hist_slabs;
         hist_slabs += batch_hist_slabs(n[k], sigma[k]);
-        lts[k] = total_levels;
-        total_levels += L[k];
+        if (L[k] > 0) {
+            if (batch_small_alphabet(L[k])) {
+                hsmall[ismall++] = k;
+            } else {
+                hbig[ibig++] = k;
+                for (uint32_t l = 0; l < L[k]; l++) {
+                    if ((1ull << l) > kBatchWarpLeaves)
+                        hbpairs[ibpair++] = k << 5 | l;
+                    else
+                        hspairs[ispair++] = k << 5 | l;
+                }
+            }
+        }
     }
     hts[count] = hist_tiles;
     sls[count] = hist_slabs;
-    lts[count] = total_levels;
     for (auto &P : plans) {
         LevelJob *pj = reinterpret_cast<LevelJob *>(ht + P.jobs_off);
         uint32_t *pts = reinterpret_cast<uint32_t *>(ht + P.ts_off);
@@ -750,7 +780,10 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
             ck(launch_batch_prepare(reinterpret_cast<const SeqJob *>(dt + seqjob_off), count,
                                     reinterpret_cast<const uint32_t *>(dt + hts_off), hist_tiles,
                                     reinterpret_cast<const uint32_t *>(dt + sls_off), hist_slabs,
-                                    reinterpret_cast<const uint32_t *>(dt + lts_off), total_levels, st));
+                                    reinterpret_cast<const uint32_t *>(dt + small_off), nsmall,
+                                    reinterpret_cast<const uint32_t *>(dt + big_off), nbig,
+                                    reinterpret_cast<const uint32_t *>(dt + bpairs_off), nbig_pairs,
+                                    reinterpret_cast<const uint32_t *>(dt + spairs_off), nsmall_pairs, st));
         }
         for (size_t q = 0; q < plans.size(); q++) {
             const LaunchPlan &P = plans[q];

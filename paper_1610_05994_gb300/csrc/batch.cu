@@ -246,12 +246,14 @@ __device__ __forceinline__ void cta_scan(uint64_t count, Val value, Out out, uin
     }
 }
 
-// Node starts of every sequence: CTA k scans sequence k's histogram into Hex
-// (2^L + 1 entries, bins at and above sigma count 0).
-__global__ void __launch_bounds__(kBatchThreads) batch_starts_kernel(const SeqJob *__restrict__ jobs) {
+// Node starts of the sequences with large alphabets: CTA b scans sequence
+// seqs[b]'s histogram into Hex (2^L + 1 entries, bins at and above sigma
+// count 0).
+__global__ void __launch_bounds__(kBatchThreads) batch_starts_kernel(const SeqJob *__restrict__ jobs,
+                                                                     const uint32_t *__restrict__ seqs) {
     __shared__ uint64_t s_warp[33];
     __shared__ uint64_t seg[kSeg];
-    const SeqJob &J = jobs[blockIdx.x];
+    const SeqJob &J = jobs[seqs[blockIdx.x]];
     if (J.L == 0) return;
     const uint64_t *hist = J.hist;
     const uint64_t sigma = J.sigma;
@@ -260,35 +262,116 @@ __global__ void __launch_bounds__(kBatchThreads) batch_starts_kernel(const SeqJo
              [&](uint64_t c, uint64_t v) { hex[c] = v; }, seg, s_warp);
 }
 
-// Node tables of every (sequence, level): CTA b takes one pair, found in the
-// prefix lvl_start of the sequences' level counts.  Same formulas as the
-// single-sequence node_tables_kernel: the zeros of node v are the symbols of
-// its left child, OB = ones before the node's start, ZE = zeros up to its end.
+// Exclusive scan over a warp of one value per lane; `total` gets the sum.
+__device__ __forceinline__ uint64_t warp_scan_u64(uint64_t v, uint64_t &total) {
+    const int lane = threadIdx.x & 31;
+    uint64_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+// Node tables of level l of one sequence by one warp (each lane a
+// contiguous block of nodes, a warp scan between the blocks).  The node
+// tables follow the single-sequence node_tables_kernel: the zeros of node v
+// are the symbols of its left child, OB = ones before the node's start,
+// ZE = zeros up to its end.  Hex is read through L2 (the same warp may just
+// have written it).
+__device__ __forceinline__ void warp_tables(const SeqJob &J, uint32_t l) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nodes = 1u << l, sh = J.L - l;
+    const uint64_t *hex = J.hex;
+    uint64_t *obl = J.ob + (nodes - 1), *zel = J.ze + (nodes - 1);
+    const uint32_t m = (nodes + 31) / 32;
+    const uint32_t v0 = min(lane * m, nodes), v1 = min(v0 + m, nodes);
+    uint64_t sum = 0;
+    for (uint32_t v = v0; v < v1; v++)
+        sum += __ldcg(hex + ((2 * (uint64_t)v + 1) << (sh - 1))) - __ldcg(hex + ((uint64_t)v << sh));
+    uint64_t total;
+    uint64_t zb = warp_scan_u64(sum, total);
+    for (uint32_t v = v0; v < v1; v++) {
+        const uint64_t h0 = __ldcg(hex + ((uint64_t)v << sh)), h1 = __ldcg(hex + ((2 * (uint64_t)v + 1) << (sh - 1)));
+        obl[v] = h0 - zb;
+        zel[v] = zb + (h1 - h0);
+        zb += h1 - h0;
+    }
+}
+
+// Node tables of the sequences with large alphabets, pairs p = sequence << 5
+// | level: CTAs [0, nbig) take one deep level each (big_pairs, the CTA scans
+// the level's nodes); the CTAs after them take kBatchThreads / 32 shallow
+// levels each, one per warp (small_pairs).
 __global__ void __launch_bounds__(kBatchThreads) batch_tables_kernel(const SeqJob *__restrict__ jobs,
-                                                                     const uint32_t *__restrict__ lvl_start,
-                                                                     uint32_t nseq) {
+                                                                     const uint32_t *__restrict__ big_pairs,
+                                                                     uint32_t nbig,
+                                                                     const uint32_t *__restrict__ small_pairs,
+                                                                     uint32_t nsmall) {
     __shared__ uint64_t s_warp[33];
     __shared__ uint64_t seg[kSeg];
-    const uint32_t k = find_seq(lvl_start, nseq, blockIdx.x);
-    const SeqJob &J = jobs[k];
-    const uint32_t l = blockIdx.x - lvl_start[k];
+    if (blockIdx.x >= nbig) {
+        const uint32_t w = (blockIdx.x - nbig) * (kBatchThreads / 32) + (threadIdx.x >> 5);
+        if (w >= nsmall) return;
+        const uint32_t pr = small_pairs[w];
+        const SeqJob &J = jobs[pr >> 5];
+        if ((pr & 31u) < J.L) warp_tables(J, pr & 31u);
+        return;
+    }
+    const uint32_t pr = big_pairs[blockIdx.x];
+    const SeqJob &J = jobs[pr >> 5];
+    const uint32_t l = pr & 31u;
     if (l >= J.L) return;
     const uint64_t nodes = 1ull << l;
     const uint32_t sh = J.L - l;  // >= 1
     const uint64_t *hex = J.hex;
     uint64_t *obl = J.ob + (nodes - 1), *zel = J.ze + (nodes - 1);
-    auto zeros = [&](uint64_t v) { return hex[(2 * v + 1) << (sh - 1)] - hex[(2 * v) << (sh - 1)]; };
-    cta_scan(nodes, zeros,
+    cta_scan(nodes, [&](uint64_t v) { return hex[(2 * v + 1) << (sh - 1)] - hex[v << sh]; },
              [&](uint64_t v, uint64_t zb) {
-                 obl[v] = hex[v << sh] - zb;
-                 zel[v] = zb + zeros(v);
+                 const uint64_t h0 = hex[v << sh], h1 = hex[(2 * v + 1) << (sh - 1)];
+                 obl[v] = h0 - zb;
+                 zel[v] = zb + (h1 - h0);
              },
              seg, s_warp);
 }
 
+// Node starts and node tables of the sequences with small alphabets
+// (2^L <= kBatchWarpLeaves): one warp per sequence seqs[w], each lane a
+// contiguous block of leaves, a warp scan between the blocks, then every
+// level's tables by the same warp.
+__global__ void __launch_bounds__(kBatchThreads) batch_small_kernel(const SeqJob *__restrict__ jobs,
+                                                                    const uint32_t *__restrict__ seqs,
+                                                                    uint32_t count) {
+    const uint32_t w = blockIdx.x * (kBatchThreads / 32) + (threadIdx.x >> 5);
+    if (w >= count) return;
+    const uint32_t lane = threadIdx.x & 31;
+    const SeqJob &J = jobs[seqs[w]];
+    const uint32_t L = J.L;
+    if (L == 0) return;
+    const uint64_t sigma = J.sigma;
+    const uint32_t leaves = 1u << L;
+    uint64_t *hex = J.hex;
+    const uint32_t m = (leaves + 1 + 31) / 32;  // entries per lane
+    const uint32_t c0 = lane * m, c1 = min(c0 + m, leaves + 1);
+    uint64_t sum = 0;
+    for (uint32_t c = c0; c < c1; c++) sum += c < sigma ? J.hist[c] : 0ull;
+    uint64_t total;
+    uint64_t run = warp_scan_u64(sum, total);
+    for (uint32_t c = c0; c < c1; c++) {
+        hex[c] = run;
+        run += c < sigma ? J.hist[c] : 0ull;
+    }
+    __syncwarp();
+    for (uint32_t l = 0; l < L; l++) warp_tables(J, l);
+}
+
 cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32_t *hist_tile_start,
                                  uint32_t hist_tiles, const uint32_t *slab_start, uint32_t slabs,
-                                 const uint32_t *lvl_start, uint32_t total_levels, cudaStream_t st) {
+                                 const uint32_t *small_seqs, uint32_t nsmall, const uint32_t *big_seqs,
+                                 uint32_t nbig, const uint32_t *big_pairs, uint32_t nbig_pairs,
+                                 const uint32_t *small_pairs, uint32_t nsmall_pairs, cudaStream_t st) {
     if (nseq == 0) return cudaSuccess;
     batch_clear_err_kernel<<<(nseq + 255) / 256, 256, 0, st>>>(jobs, nseq);
     note_launches(1);
@@ -323,10 +406,19 @@ cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32
         batch_hist_packed_kernel<<<slabs, kPackedThreads, smem, st>>>(jobs, slab_start, nseq);
         note_launches(1);
     }
-    batch_starts_kernel<<<nseq, kBatchThreads, 0, st>>>(jobs);
-    note_launches(1);
-    if (total_levels) {
-        batch_tables_kernel<<<total_levels, kBatchThreads, 0, st>>>(jobs, lvl_start, nseq);
+    if (nsmall) {
+        constexpr uint32_t kWarps = kBatchThreads / 32;
+        batch_small_kernel<<<(nsmall + kWarps - 1) / kWarps, kBatchThreads, 0, st>>>(jobs, small_seqs, nsmall);
+        note_launches(1);
+    }
+    if (nbig) {
+        batch_starts_kernel<<<nbig, kBatchThreads, 0, st>>>(jobs, big_seqs);
+        note_launches(1);
+    }
+    if (nbig_pairs + nsmall_pairs) {
+        constexpr uint32_t kWarps = kBatchThreads / 32;
+        batch_tables_kernel<<<nbig_pairs + (nsmall_pairs + kWarps - 1) / kWarps, kBatchThreads, 0, st>>>(
+            jobs, big_pairs, nbig_pairs, small_pairs, nsmall_pairs);
         note_launches(1);
     }
     return cudaGetLastError();

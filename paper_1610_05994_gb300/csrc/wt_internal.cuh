@@ -310,9 +310,17 @@ struct SeqJob {
 // very large alphabets) and slabs of the packed kernel (the rest).
 uint32_t batch_hist_tiles(uint64_t n, uint64_t sigma);
 uint32_t batch_hist_slabs(uint64_t n, uint64_t sigma);
+// Node starts and tables: sequences with 2^L <= kBatchWarpLeaves take one
+// warp each (small_seqs); the others one CTA for the starts (big_seqs), one
+// CTA per level with more than kBatchWarpLeaves nodes (big_pairs) and one
+// warp per other level (small_pairs); a pair is sequence << 5 | level.
+constexpr uint32_t kBatchWarpLeaves = 1024;
+inline bool batch_small_alphabet(uint32_t L) { return (1ull << L) <= kBatchWarpLeaves; }
 cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32_t *hist_tile_start,
                                  uint32_t hist_tiles, const uint32_t *slab_start, uint32_t slabs,
-                                 const uint32_t *lvl_start, uint32_t total_levels, cudaStream_t st);
+                                 const uint32_t *small_seqs, uint32_t nsmall, const uint32_t *big_seqs,
+                                 uint32_t nbig, const uint32_t *big_pairs, uint32_t nbig_pairs,
+                                 const uint32_t *small_pairs, uint32_t nsmall_pairs, cudaStream_t st);
 
 // Kernel (e): queries.
 cudaError_t launch_access(const TreeDesc *t, const uint64_t *i, uint64_t m, uint32_t *out, cudaStream_t st);

@@ -126,6 +126,85 @@ def zipf(n: int, sigma: int, alpha: float, seed: int, dtype=None) -> np.ndarray:
     return _parallel_fill(n, dtype, fill)
 
 
+# ------------------------------------------------ locality stress inputs
+#
+# The paper's locality experiment (Section 4, the cont and rand data sets):
+# n symbols over sigma codes, each code written n / sigma times.  cont puts
+# them in code order (every level of the tree sees long runs of one node);
+# rand puts the same multiset at random positions.  Here rand[j] =
+# cont[pi(j)] for a seeded bijection pi of [0, n): on k-bit integers (2^k >=
+# n) an offset by the seed, then three rounds of an xorshift and a multiply
+# by an odd constant mod 2^k (each step invertible), cycle-walked into
+# [0, n).  Both a numpy and a torch form are given; they agree bit for bit.
+
+_LOC_MULS = (0x9E3779B1, 0x85EBCA6B, 0xC2B2AE35)
+
+
+def _loc_bits(n: int) -> int:
+    return max(1, (n - 1).bit_length())
+
+
+def _loc_round(x, k: int, seed: int, xp_and, xp_xor, xp_shr, xp_mul, xp_add):
+    m = (1 << k) - 1
+    x = xp_and(xp_add(x, seed & m), m)
+    for c in _LOC_MULS:
+        x = xp_xor(x, xp_shr(x, max(1, k // 2)))
+        x = xp_and(xp_mul(x, c), m)
+    return xp_xor(x, xp_shr(x, max(1, (k + 1) // 2)))
+
+
+def locality_positions(j: np.ndarray, n: int, seed: int) -> np.ndarray:
+    """pi(j) for positions j of [0, n) (numpy, uint64)."""
+    k = _loc_bits(n)
+    u = np.uint64
+    with np.errstate(over="ignore"):
+        f = lambda x: _loc_round(x, k, seed, lambda a, b: a & u(b), lambda a, b: a ^ b, lambda a, b: a >> u(b),
+                                 lambda a, b: a * u(b), lambda a, b: a + u(b))
+        x = f(j.astype(np.uint64))
+        out = x >= u(n)
+        while out.any():
+            x[out] = f(x[out])
+            out = x >= u(n)
+    return x
+
+
+def locality(n: int, sigma: int, kind: str, seed: int, dtype=np.uint32) -> np.ndarray:
+    """The cont or rand sequence (numpy): code floor(q * sigma / n) at
+    q = j (cont) or q = pi(j) (rand)."""
+    s = np.uint64(sigma)
+
+    def fill(st, c):
+        j = np.arange(st, st + c, dtype=np.uint64)
+        q = j if kind == "cont" else locality_positions(j, n, seed)
+        return ((q * s) // np.uint64(n)).astype(dtype)
+
+    return _parallel_fill(n, dtype, fill)
+
+
+def locality_torch(n: int, sigma: int, kind: str, seed: int, device, dtype=None):
+    """The same sequence generated by torch on `device` (int32 codes, or
+    `dtype`), for sizes whose host generation would take long."""
+    import torch
+    k = _loc_bits(n)
+    j = torch.arange(n, dtype=torch.int64, device=device)
+    if kind == "cont":
+        q = j
+    else:
+        f = lambda x: _loc_round(x, k, seed, lambda a, b: a & b, lambda a, b: a ^ b, lambda a, b: a >> b,
+                                 lambda a, b: a * b, lambda a, b: a + b)
+        q = f(j)
+        del j
+        out = q >= n
+        while bool(out.any()):
+            q = torch.where(out, f(q), q)
+            out = q >= n
+    codes = torch.div(q * sigma, n, rounding_mode="floor")
+    return codes.to(dtype or torch.int32)
+
+
+LOCALITY_SIZES = tuple(range(4, 15, 2))   # sigma = 2^y, y in {4, 6, ..., 14}
+
+
 # ----------------------------------------------------------- named workloads
 
 @dataclass(frozen=True)
