@@ -66,15 +66,22 @@ struct LwCfg {
     static constexpr int kMinCtas = 4;                                // resident CTAs per SM
 };
 
-constexpr uint32_t kScanSeg = 4096;  // tiles per segment of the prefix scan
+constexpr uint32_t kScanSeg = 4096;  // chunks per segment of the prefix scan
+// The counts and prefixes are kept per warp range (a chunk, kLwWarpBytes of
+// P_l; kLwWarps chunks per tile), so that every warp of the pass knows the
+// ones before its own range without exchanging counts with the others.
+constexpr uint32_t kLwChunks = kLwWarps;
+constexpr uint32_t kLwPreCopy = kLwChunks + 2;  // prefixes copied per tile (80 bytes)
 
 uint32_t lw_tile_elems(int width) { return kLwTileBytes / (uint32_t)width; }
-size_t lw_counts_bytes(uint64_t n, int width) { return (size_t)ceil_div(n, lw_tile_elems(width)) * 4; }
-// ntiles + 2 prefixes (the pass reads them in aligned pairs), then one sum per
-// scan segment.
+size_t lw_counts_bytes(uint64_t n, int width) {
+    return (size_t)ceil_div(n, lw_tile_elems(width)) * kLwChunks * 4;
+}
+// A prefix per chunk, the total and one spare (the pass copies kLwPreCopy
+// per tile), then one sum per scan segment.
 size_t lw_prefix_bytes(uint64_t n, int width) {
-    const uint64_t nt = ceil_div(n, lw_tile_elems(width));
-    return (size_t)(nt + 2 + ceil_div(nt, kScanSeg) + 1) * 8;
+    const uint64_t nc = ceil_div(n, lw_tile_elems(width)) * kLwChunks;
+    return (size_t)(nc + 2 + ceil_div(nc, kScanSeg) + 1) * 8;
 }
 
 struct LevelLaunch {
@@ -141,7 +148,7 @@ __device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Writes one run of the split copy to global memory: bytes [g0, g0 + len)
@@ -167,8 +174,8 @@ __device__ __forceinline__ void store_run(uintptr_t g0, uint32_t len, const unsi
 
 // ---------------------------------------------------------------- counts
 
-// The level-l ones of every tile of P_l: symbols with bit L - 1 - l set.
-// One warp per tile, the warps of the grid striding over the tiles together
+// The level-l ones of every chunk of P_l: symbols with bit L - 1 - l set.
+// One warp per tile (kLwChunks chunks), the warps of the grid striding over the tiles together
 // (a window of consecutive tiles in flight, eight 16-byte loads per lane);
 // each warp finds a tile's job by binary search from its previous one.
 constexpr int kCountThreads = 256;
@@ -200,7 +207,11 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(LevelLaunch a) {
         const uint64_t base = (uint64_t)tile * Cfg::kTile;
         const uint32_t cnt = (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
         const uint32_t bsh = J.L - bsh_l;
-        uint32_t c = 0;
+        constexpr int kPerChunk = kVecs / (int)kLwChunks;  // 16-byte loads per lane per chunk
+        constexpr uint32_t kChunkSyms = kLwWarpBytes / sizeof(Sym);
+        uint32_t c[kLwChunks];
+#pragma unroll
+        for (int j = 0; j < (int)kLwChunks; j++) c[j] = 0;
         if (cnt == Cfg::kTile && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
             const uint4 *v = reinterpret_cast<const uint4 *>(S + base) + lane;
 #pragma unroll
@@ -211,26 +222,34 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(LevelLaunch a) {
 #pragma unroll
                 for (int r = 0; r < 8; r++) {
                     const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
-                    c += __popc(chunk_bits<Sym>(x, bsh));
+                    c[(h + r) / kPerChunk] += __popc(chunk_bits<Sym>(x, bsh));
                 }
             }
         } else {
-            for (uint32_t p = lane; p < cnt; p += 32) c += ((uint32_t)S[base + p] >> bsh) & 1u;
+#pragma unroll
+            for (int j = 0; j < (int)kLwChunks; j++)
+                for (uint32_t p = j * kChunkSyms + lane; p < min(cnt, (j + 1) * kChunkSyms); p += 32)
+                    c[j] += ((uint32_t)S[base + p] >> bsh) & 1u;
         }
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0) J.cnt[tile] = c;
+        uint32_t mine = 0;  // lane j < kLwChunks stores chunk j's count
+#pragma unroll
+        for (int j = 0; j < (int)kLwChunks; j++) {
+            const uint32_t t = __reduce_add_sync(0xffffffffu, c[j]);
+            if (lane == j) mine = t;
+        }
+        if (lane < (int)kLwChunks) J.cnt[(size_t)tile * kLwChunks + lane] = mine;
     }
 }
 
-// Tile prefixes of every job, pre[t] = ones of the job's tiles before t, in
-// two launches over segments of kScanSeg tiles (CTA x = job * segs + seg):
+// Chunk prefixes of every job, pre[c] = ones of the job's chunks before c, in
+// two launches over segments of kScanSeg chunks (CTA x = job * segs + seg):
 // the sums of the segments, then each segment's scan from the sums of the
 // segments before it.
 __global__ void __launch_bounds__(1024) scan_sums_kernel(LevelLaunch a) {
     __shared__ uint32_t part[32];
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
     const LevelJob &J = a.jobs[job];
-    const uint32_t nt = J.ntiles;
+    const uint32_t nt = J.ntiles * kLwChunks;  // chunks
     if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t c = 0;
@@ -254,7 +273,7 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     __shared__ uint64_t s_base;
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
     const LevelJob &J = a.jobs[job];
-    const uint32_t nt = J.ntiles;
+    const uint32_t nt = J.ntiles * kLwChunks;  // chunks
     if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (warp == 0) {
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
         for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
         if (lane == 0) s_base = b;
     }
-    // Four consecutive tiles per thread.
+    // Four consecutive chunks per thread.
     const uint32_t t0 = seg * kScanSeg + 4 * tid;
     uint32_t c[4];
 #pragma unroll
@@ -295,30 +314,28 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
         if (t0 + j < nt) J.pre[t0 + j] = run;
         run += c[j];
     }
-    if (t0 < nt && nt <= t0 + 4) J.pre[nt] = run;  // the total, read with the last tile's pair
+    if (t0 < nt && nt <= t0 + 4) J.pre[nt] = run;  // the total, read with the last tile's prefixes
 }
 
 // ------------------------------------------------------------------ pass
 
 // One input stage: a tile, its sequence, its prefix, and its symbols.
 struct __align__(16) LwStage {
+    uint64_t pre[kLwPreCopy];  // pre[c] for the tile's chunks c and the next tile's first (one copy)
     LevelJob J;
-    uint64_t pre2[2];      // pre[tile & ~1], pre[tile | 1] (one 16-byte copy)
-    uint32_t tile;         // kNoTile: this CTA has no more tiles
-    uint32_t full;         // a whole tile, 16-byte aligned: its symbols came in by bulk copy
+    uint32_t tile;             // kNoTile: this CTA has no more tiles
+    uint32_t full;             // a whole tile, 16-byte aligned: its symbols came in by bulk copy
 };
 
 struct LwShared {
     LwStage st[kLwStages];
     LevelJob job;                          // the job of the claimer's latest tile
     uint64_t bar[kLwStages];               // a stage is in place
-    uint32_t wtot[kLwWarps];               // ones of each warp's range
-    uint32_t blkw[kLwTileBytes / 512];     // ones before each rank block within its warp's range
 };
 
 // Claims this CTA's tile g into stage s (warp 0, all lanes): the stage
-// record (copied by the lanes) and, by bulk copy, the prefix pair and (whole
-// aligned tiles) the symbols.  k and have_job are the same in every lane.
+// record (copied by the lanes) and, by bulk copy, the tile's chunk prefixes
+// and (whole aligned tiles) the symbols.  k and have_job are the same in every lane.
 template <typename Sym>
 __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, unsigned char *in, int s, uint32_t g,
                                          uint32_t g_end, uint32_t &k, bool &have_job) {
@@ -353,28 +370,47 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
         S.tile = tile;
         S.full = full;
         fence_proxy_async_smem();
-        mbar_arrive_expect(&sh.bar[s], 16 + (full ? kLwTileBytes : 0));
-        bulk_copy(S.pre2, S.J.pre + (tile & ~1u), 16, &sh.bar[s]);
+        mbar_arrive_expect(&sh.bar[s], kLwPreCopy * 8 + (full ? kLwTileBytes : 0));
+        bulk_copy(S.pre, S.J.pre + (size_t)tile * kLwChunks, kLwPreCopy * 8, &sh.bar[s]);
         if (full)
             bulk_copy(in + s * kLwTileBytes, static_cast<const Sym *>(S.J.cur) + base, kLwTileBytes, &sh.bar[s]);
     }
 }
 
-// One tile: count, directory, placement and the bulk stores (all threads).
-// kWhole: the tile holds kTile symbols (no bound checks per symbol).
+// What a tile sends out by bulk store once every thread has written the
+// shared copies.
+struct LwOut {
+    unsigned char *bm_dst;
+    uint32_t bm_bytes;
+    bool runs;               // one node: a zeros run and a ones run
+    uintptr_t gz_b, go_b;    // their destinations
+    uint32_t zlen, olen;     // their bytes
+    uint32_t offz, B1;       // their places in the split copy
+};
+
+// One tile: count, directory and placement into the shared copies, which
+// the caller sends out with lw_store after its next barrier (all threads).
+// Each warp works from the prefix of its own chunk, so no counts are
+// exchanged between the warps.  kWhole: the tile holds kTile symbols (no
+// bound checks per symbol).
 template <typename Sym, bool kWhole>
-__device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, LwShared &sh, const unsigned char *buf,
-                                        unsigned char *split, unsigned char *bits, bool &bad) {
+__device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, const unsigned char *buf,
+                                        unsigned char *split, unsigned char *bits, bool &bad, LwOut &out) {
     using Cfg = LwCfg<Sym>;
     constexpr int kSps = Cfg::kSps;
     constexpr int kW = Cfg::kW;
+    constexpr uint32_t kWarpSyms = kLwWarpBytes / kW;
+    constexpr uint32_t kBlockBytes = 512 * kW;  // a rank block of the bitmap, in bytes of P_l
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t l = a.l;
     const LevelJob &J = S.J;
     const uint32_t tile = S.tile;
     const uint64_t base = (uint64_t)tile * Cfg::kTile;
     const uint32_t cnt = kWhole ? Cfg::kTile : (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
-    const uint64_t P = S.pre2[tile & 1];  // ones before the tile
+    const uint64_t P = S.pre[0];                                 // ones before the tile
+    const uint32_t wx = (uint32_t)(S.pre[warp] - P);             // ones before this warp's range
+    const uint32_t tile_ones = (uint32_t)(S.pre[kLwChunks] - P);
+    const uint32_t Zt = cnt - tile_ones;
     const uint32_t bsh = J.L - 1 - l;     // the level-l bit
     const bool has_next = J.nxt != nullptr;
 
@@ -391,29 +427,6 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     }
     uint32_t tpk;
     const uint32_t lpk = warp_excl_scan(cpk, lane, tpk);
-    if (lane == 0) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int st = 0; st < kLwSteps; st++) {
-            const uint32_t q = warp * kLwWarpBytes + st * 512;
-            if (q % (512 * kW) == 0) sh.blkw[q / (512 * kW)] = run;
-            run += (tpk >> (16 * st)) & 0xffffu;
-        }
-        sh.wtot[warp] = run;
-    }
-    // The bulk stores of tile i - 2 (the copies this tile reuses) must
-    // have read them before the barrier.
-    if (tid == 0 || tid == 32) bulk_wait_read1();
-    __syncthreads();
-
-    uint32_t wx = 0, tile_ones = 0;  // ones before this warp's range; in the tile
-#pragma unroll
-    for (int w = 0; w < kLwWarps; w++) {
-        const uint32_t y = sh.wtot[w];
-        wx += w < warp ? y : 0u;
-        tile_ones += y;
-    }
-    const uint32_t Zt = cnt - tile_ones;
 
     // The bitmap copy.
 #pragma unroll
@@ -427,38 +440,57 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
         }
     }
 
-    // Directory (warp 2): R and Hy at the tile's rank blocks, the select
-    // samples that fall in the tile (a ballot over the block prefixes
-    // finds each sample's block), the level totals after the last tile.
-    if (warp == 2) {
+    // Directory of this warp's range (lane 0): R and Hy at the rank blocks
+    // that start in it, the select samples whose one (zero) lies in it (the
+    // sample's block is the last one starting at or before it), and after
+    // the last tile the level totals.
+    if (lane == 0) {
         const uint64_t block0 = base >> 9;
-        uint32_t blk = tile_ones;  // lane b < kBlocks: ones before rank block b of the tile
-        if (lane < (int)Cfg::kBlocks) {
-            const uint32_t w = ((uint32_t)lane * 512 * kW) / kLwWarpBytes;
-            uint32_t s0 = 0;
-            for (uint32_t v = 0; v < w; v++) s0 += sh.wtot[v];
-            blk = s0 + sh.blkw[lane];
-            const uint64_t block = block0 + lane;
-            if (block < J.nblocks) {
-                const uint64_t v = P + blk;
+        const uint32_t wsym0 = warp * kWarpSyms;
+        const uint32_t wv = cnt > wsym0 ? min(cnt - wsym0, kWarpSyms) : 0u;  // symbols in the range
+        uint32_t c[kLwSteps], wones = 0;
+#pragma unroll
+        for (int st = 0; st < kLwSteps; st++) {
+            c[st] = (tpk >> (16 * st)) & 0xffffu;
+            wones += c[st];
+        }
+        uint32_t run = 0;
+#pragma unroll
+        for (int st = 0; st < kLwSteps; st++) {
+            const uint32_t q = warp * kLwWarpBytes + st * 512;
+            const uint64_t block = block0 + q / kBlockBytes;
+            if (q % kBlockBytes == 0 && block < J.nblocks) {
+                const uint64_t v = P + wx + run;
                 J.lv.R[block] = (uint32_t)v;
                 if ((block & kBlocksPerSpanMask) == 0) J.lv.Hy[block >> (kSpanShift - 9)] = v;
             }
+            run += c[st];
         }
-        const bool in = lane < (int)Cfg::kBlocks;
-        for (uint64_t k2 = ceil_div(P, kSample); k2 * kSample < P + tile_ones; k2++) {
-            const uint32_t r = (uint32_t)(k2 * kSample - P);
-            const uint32_t b = __popc(__ballot_sync(0xffffffffu, in && blk <= r)) - 1;
-            if (lane == 0) J.lv.S1[k2] = (uint32_t)(block0 + b);
+        for (uint64_t k2 = ceil_div(P + wx, kSample); k2 * kSample < P + wx + wones; k2++) {
+            const uint32_t r = (uint32_t)(k2 * kSample - P);  // ones of the tile before the sample's one
+            uint32_t b = wsym0 / 512, o = wx;
+#pragma unroll
+            for (int st = 0; st < kLwSteps; st++) {
+                const uint32_t q = warp * kLwWarpBytes + st * 512;
+                if (st > 0 && q % kBlockBytes == 0 && o <= r) b = q / kBlockBytes;
+                o += c[st];
+            }
+            J.lv.S1[k2] = (uint32_t)(block0 + b);
         }
-        const uint64_t zp = base - P;
-        const uint32_t zb = (uint32_t)lane * 512u - blk;  // zeros before block `lane`
-        for (uint64_t k2 = ceil_div(zp, kSample); k2 * kSample < zp + Zt; k2++) {
+        const uint64_t zp = base - P;           // zeros before the tile
+        const uint32_t zw = wsym0 - wx;         // zeros of the tile before this warp's range
+        for (uint64_t k2 = ceil_div(zp + zw, kSample); k2 * kSample < zp + zw + (wv - wones); k2++) {
             const uint32_t r = (uint32_t)(k2 * kSample - zp);
-            const uint32_t b = __popc(__ballot_sync(0xffffffffu, in && zb <= r)) - 1;
-            if (lane == 0) J.lv.S0[k2] = (uint32_t)(block0 + b);
+            uint32_t b = wsym0 / 512, o = wx;
+#pragma unroll
+            for (int st = 0; st < kLwSteps; st++) {
+                const uint32_t q = warp * kLwWarpBytes + st * 512;
+                if (st > 0 && q % kBlockBytes == 0 && q / kW - o <= r) b = q / kBlockBytes;
+                o += c[st];
+            }
+            J.lv.S0[k2] = (uint32_t)(block0 + b);
         }
-        if (lane == 0 && tile == J.ntiles - 1) {
+        if (tid == 0 && tile == J.ntiles - 1) {
             const uint64_t total = P + tile_ones;
             J.lv.R[J.nblocks] = (uint32_t)total;
             J.lv.Hy[J.nspans] = total;
@@ -548,14 +580,27 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
         }
     }
     fence_proxy_async_smem();  // the bitmap and split copies are read by bulk stores
-    __syncthreads();
+    out.bm_dst = bm_dst;
+    out.bm_bytes = bm_bytes;
+    out.runs = runs;
+    out.gz_b = gz_b;
+    out.go_b = go_b;
+    out.zlen = Zt * kW;
+    out.olen = tile_ones * kW;
+    out.offz = offz;
+    out.B1 = B1;
+}
 
-    if (tid == 32) bulk_store(bm_dst, bits, bm_bytes);
-    if (runs) {
+// The bulk stores of a tile (threads 0..63, after the barrier that follows
+// lw_tile): the bitmap copy, and for a one-node tile its two runs.
+__device__ __forceinline__ void lw_store(const LwOut &o, const unsigned char *split, const unsigned char *bits) {
+    const int tid = threadIdx.x;
+    if (tid == 32) bulk_store(o.bm_dst, bits, o.bm_bytes);
+    if (o.runs) {
         if (tid < 32)
-            store_run(gz_b, Zt * kW, split + offz, tid);
+            store_run(o.gz_b, o.zlen, split + o.offz, tid);
         else if (tid < 64)
-            store_run(go_b, tile_ones * kW, split + B1, tid - 32);
+            store_run(o.go_b, o.olen, split + o.B1, tid - 32);
     }
 }
 
@@ -587,14 +632,12 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
     __syncthreads();
 
     bool failed = false, bad = false;
-    for (uint32_t i = 0;; i++) {
+    // One barrier per tile: it publishes tile i's shared copies to the
+    // threads that bulk-store them and stage i + 1 to every thread.
+    if (__syncthreads_or(!mbar_wait(&sh.bar[0], 0u))) failed = true;
+    for (uint32_t i = 0; !failed; i++) {
         const int s = (int)(i % kLwStages), par = (int)(i & 1);
-        const bool ok = mbar_wait(&sh.bar[s], (i / kLwStages) & 1u);
         const LwStage &S = sh.st[s];
-        if (__syncthreads_or(!ok)) {  // a give-up is taken by every thread
-            failed = true;
-            break;
-        }
         if (S.tile == kNoTile) break;  // every thread reads the same record
         // Stage (i + 3) % 4 held tile i - 1, which is done: claim tile i + 3
         // into it while the other warps count this one.
@@ -616,10 +659,21 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
             for (uint32_t p = tid; p < Cfg::kTile; p += kLwThreads) sb[p] = p < cnt ? src[base + p] : (Sym)0;
             __syncthreads();
         }
+        LwOut out;
         if (cnt == Cfg::kTile)
-            lw_tile<Sym, true>(a, S, sh, buf, split, bits, bad);
+            lw_tile<Sym, true>(a, S, buf, split, bits, bad, out);
         else
-            lw_tile<Sym, false>(a, S, sh, buf, split, bits, bad);
+            lw_tile<Sym, false>(a, S, buf, split, bits, bad, out);
+        // The copies of the other parity (tile i - 1) are reused by tile
+        // i + 1: their bulk stores must have read them before the barrier.
+        if (tid == 0 || tid == 32) bulk_wait_read0();
+        const uint32_t i1 = i + 1;
+        const bool ok = mbar_wait(&sh.bar[i1 % kLwStages], (i1 / kLwStages) & 1u);
+        if (__syncthreads_or(!ok)) {  // a give-up is taken by every thread
+            failed = true;
+            break;
+        }
+        lw_store(out, split, bits);
         if (tid == 0 || tid == 32) bulk_commit();
     }
     if (tid == 0 || tid == 32) bulk_wait_all();
@@ -689,7 +743,7 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.njobs = njobs;
     a.total_tiles = total_tiles;
     a.l = l;
-    a.segs = (uint32_t)ceil_div(max_job_tiles ? max_job_tiles : 1, kScanSeg);
+    a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * kLwChunks, kScanSeg);
     a.err = err;
     switch (width) {
         case 1: return launch_lw<uint8_t>(a, st);
