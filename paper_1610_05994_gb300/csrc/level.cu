@@ -1,10 +1,8 @@
 // level.cu -- kernels (b) + (c): the fused per-level pass of the level-wise
-// build.
+// build, with its count pass and prefix scan.
 //
 // One pass over P_l (the symbols in level-l order) does, per tile of 8 KB:
-//   (b) packs the level-l bit of every symbol into the bitmap and writes the
-//       rank directory (R, Hy) and the select samples (S1, S0) from the ones
-//       before the tile and the tile's own counts;
+//   (b) packs the level-l bit of every symbol into the bitmap;
 //   (c) places every symbol at its position in P_{l+1}:
 //          bit 0:  dst = zeros_before(p) + OB_l[v]
 //          bit 1:  dst = ones_before(p)  + ZE_l[v]
@@ -14,18 +12,22 @@
 //       Section 3.1) written as a closed form of two prefix counts, so one
 //       global scan serves every node of the level.
 //
-// Where the ones before a tile come from: a count pass reads P_l at full
-// bandwidth and stores the level-l ones of every tile; a segmented scan
-// turns them into each tile's prefix before the pass starts, so the tiles of
-// a pass are independent and no CTA ever waits for another.  (Counting the
-// next level's ones inside the pass, where each symbol's destination is
+// Where the ones before a position come from: a count pass reads P_l at full
+// bandwidth and stores the level-l ones of every unit (a warp's 1 KB range of
+// a tile, or a 512-symbol rank block when that is shorter); a segmented scan
+// turns them into prefixes before the pass starts.  The same scan writes the
+// level's rank directory (R, Hy) and select samples (S1, S0), since the
+// prefix at a rank block's first unit is R itself.  So the tiles of a pass
+// are independent, and inside a tile every warp starts from its own prefix:
+// no CTA waits for another and no warp for the others' counts.  (Counting
+// the next level's ones inside the pass, where each symbol's destination is
 // known, cost more instructions than the extra read.)
 //
 // GPU structure: a persistent CTA of 256 threads takes a contiguous range of
 // tiles and keeps four stages: warp 0 claims a tile three ahead and one
 // thread issues TMA bulk copies (cp.async.bulk) of its symbols and of its
-// prefix into a shared-memory stage while the CTA works on the current one.
-// Per tile:
+// unit prefixes into a shared-memory stage while the CTA works on the
+// current one.  Per tile:
 //   * a lane owns 16 consecutive bytes of each 512-byte warp step, so its
 //     level bits are 16 (8, 4) consecutive bits of the bitmap: they go to a
 //     shared-memory copy of the tile's bitmap that leaves with one bulk
@@ -38,6 +40,8 @@
 //     destination's 16-byte alignment; the aligned interior of each run
 //     leaves with one bulk store, the ragged ends with byte stores.  Tiles
 //     that span several nodes store every symbol at its own destination.
+//   * one CTA barrier per tile: it hands the tile's shared copies to the
+//     threads that bulk-store them and the next stage to every thread.
 // The only waits are on the bulk copies, bounded like every wait of the
 // library.
 #include <cuda_runtime.h>
@@ -56,6 +60,14 @@ constexpr uint32_t kLwSplitBytes = kLwTileBytes + 64;              // two runs +
 constexpr uint32_t kLwBitsBytes = kLwTileBytes / 8;                // the bitmap copy (for bytes)
 constexpr int kLwStages = 4;
 constexpr uint32_t kNoTile = 0xffffffffu;
+// The counts and prefixes are kept per unit of P_l: a warp's range or a rank
+// block of the bitmap, whichever is shorter (kLwWarpBytes or 512 symbols).
+// Every warp of the pass then reads the ones before its own range, and the
+// prefix scan reads the ones before every rank block, which is the rank
+// directory itself.
+constexpr uint32_t lw_unit_bytes(uint32_t width) { return 512 * width < kLwWarpBytes ? 512 * width : kLwWarpBytes; }
+constexpr uint32_t lw_units(uint32_t width) { return kLwTileBytes / lw_unit_bytes(width); }  // per tile
+constexpr uint32_t kLwMaxUnits = lw_units(1);
 
 template <typename Sym>
 struct LwCfg {
@@ -64,23 +76,21 @@ struct LwCfg {
     static constexpr uint32_t kTile = kLwTileBytes / kW;              // symbols per tile
     static constexpr uint32_t kBlocks = kTile / 512;                  // rank blocks per tile
     static constexpr int kMinCtas = 4;                                // resident CTAs per SM
+    static constexpr uint32_t kUnits = lw_units(sizeof(Sym));         // count units per tile
+    static constexpr uint32_t kUnitsPerWarp = kLwWarpBytes / lw_unit_bytes(sizeof(Sym));
+    static constexpr uint32_t kPreCopy = kUnits + 2;                  // prefixes copied per tile
 };
 
-constexpr uint32_t kScanSeg = 4096;  // chunks per segment of the prefix scan
-// The counts and prefixes are kept per warp range (a chunk, kLwWarpBytes of
-// P_l; kLwWarps chunks per tile), so that every warp of the pass knows the
-// ones before its own range without exchanging counts with the others.
-constexpr uint32_t kLwChunks = kLwWarps;
-constexpr uint32_t kLwPreCopy = kLwChunks + 2;  // prefixes copied per tile (80 bytes)
+constexpr uint32_t kScanSeg = 4096;  // units per segment of the prefix scan
 
 uint32_t lw_tile_elems(int width) { return kLwTileBytes / (uint32_t)width; }
 size_t lw_counts_bytes(uint64_t n, int width) {
-    return (size_t)ceil_div(n, lw_tile_elems(width)) * kLwChunks * 4;
+    return (size_t)ceil_div(n, lw_tile_elems(width)) * lw_units((uint32_t)width) * 4;
 }
-// A prefix per chunk, the total and one spare (the pass copies kLwPreCopy
-// per tile), then one sum per scan segment.
+// A prefix per unit, the total and one spare (the pass copies a tile's units
+// + 2), then one sum per scan segment.
 size_t lw_prefix_bytes(uint64_t n, int width) {
-    const uint64_t nc = ceil_div(n, lw_tile_elems(width)) * kLwChunks;
+    const uint64_t nc = ceil_div(n, lw_tile_elems(width)) * lw_units((uint32_t)width);
     return (size_t)(nc + 2 + ceil_div(nc, kScanSeg) + 1) * 8;
 }
 
@@ -89,6 +99,7 @@ struct LevelLaunch {
     const uint32_t *tile_start;  // device, njobs + 1: first global tile of each job
     uint32_t njobs, total_tiles, l;
     uint32_t segs;               // scan segments of the largest job
+    uint32_t units, upb;         // count units per tile and per rank block
     uint32_t *err;
 };
 
@@ -174,8 +185,8 @@ __device__ __forceinline__ void store_run(uintptr_t g0, uint32_t len, const unsi
 
 // ---------------------------------------------------------------- counts
 
-// The level-l ones of every chunk of P_l: symbols with bit L - 1 - l set.
-// One warp per tile (kLwChunks chunks), the warps of the grid striding over the tiles together
+// The level-l ones of every unit of P_l: symbols with bit L - 1 - l set.
+// One warp per tile (kUnits units), the warps of the grid striding over the tiles together
 // (a window of consecutive tiles in flight, eight 16-byte loads per lane);
 // each warp finds a tile's job by binary search from its previous one.
 constexpr int kCountThreads = 256;
@@ -207,11 +218,12 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(LevelLaunch a) {
         const uint64_t base = (uint64_t)tile * Cfg::kTile;
         const uint32_t cnt = (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
         const uint32_t bsh = J.L - bsh_l;
-        constexpr int kPerChunk = kVecs / (int)kLwChunks;  // 16-byte loads per lane per chunk
-        constexpr uint32_t kChunkSyms = kLwWarpBytes / sizeof(Sym);
-        uint32_t c[kLwChunks];
+        constexpr uint32_t kU = Cfg::kUnits;
+        constexpr int kPerUnit = kVecs / (int)kU;  // 16-byte loads per lane per unit
+        constexpr uint32_t kUnitSyms = Cfg::kTile / kU;
+        uint32_t c[kU];
 #pragma unroll
-        for (int j = 0; j < (int)kLwChunks; j++) c[j] = 0;
+        for (int j = 0; j < (int)kU; j++) c[j] = 0;
         if (cnt == Cfg::kTile && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
             const uint4 *v = reinterpret_cast<const uint4 *>(S + base) + lane;
 #pragma unroll
@@ -222,34 +234,34 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(LevelLaunch a) {
 #pragma unroll
                 for (int r = 0; r < 8; r++) {
                     const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
-                    c[(h + r) / kPerChunk] += __popc(chunk_bits<Sym>(x, bsh));
+                    c[(h + r) / kPerUnit] += __popc(chunk_bits<Sym>(x, bsh));
                 }
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < (int)kLwChunks; j++)
-                for (uint32_t p = j * kChunkSyms + lane; p < min(cnt, (j + 1) * kChunkSyms); p += 32)
+            for (int j = 0; j < (int)kU; j++)
+                for (uint32_t p = j * kUnitSyms + lane; p < min(cnt, (j + 1) * kUnitSyms); p += 32)
                     c[j] += ((uint32_t)S[base + p] >> bsh) & 1u;
         }
-        uint32_t mine = 0;  // lane j < kLwChunks stores chunk j's count
+        uint32_t mine = 0;  // lane j < kU stores unit j's count
 #pragma unroll
-        for (int j = 0; j < (int)kLwChunks; j++) {
+        for (int j = 0; j < (int)kU; j++) {
             const uint32_t t = __reduce_add_sync(0xffffffffu, c[j]);
             if (lane == j) mine = t;
         }
-        if (lane < (int)kLwChunks) J.cnt[(size_t)tile * kLwChunks + lane] = mine;
+        if (lane < (int)kU) J.cnt[(size_t)tile * kU + lane] = mine;
     }
 }
 
-// Chunk prefixes of every job, pre[c] = ones of the job's chunks before c, in
-// two launches over segments of kScanSeg chunks (CTA x = job * segs + seg):
+// Unit prefixes of every job, pre[u] = ones of the job's units before u, in
+// two launches over segments of kScanSeg units (CTA x = job * segs + seg):
 // the sums of the segments, then each segment's scan from the sums of the
 // segments before it.
 __global__ void __launch_bounds__(1024) scan_sums_kernel(LevelLaunch a) {
     __shared__ uint32_t part[32];
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
     const LevelJob &J = a.jobs[job];
-    const uint32_t nt = J.ntiles * kLwChunks;  // chunks
+    const uint32_t nt = J.ntiles * a.units;  // units
     if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t c = 0;
@@ -273,7 +285,7 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     __shared__ uint64_t s_base;
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
     const LevelJob &J = a.jobs[job];
-    const uint32_t nt = J.ntiles * kLwChunks;  // chunks
+    const uint32_t nt = J.ntiles * a.units;  // units
     if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (warp == 0) {
@@ -309,19 +321,41 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     }
     __syncthreads();
     uint64_t run = s_base + s_warp[warp] + inc - sum;
+    // The rank directory of level l (Section 2.2's R, Hy and select
+    // samples) from the same prefixes: a rank block starts at every upb-th
+    // unit; the samples of the ones (zeros) that fall in a block point to it.
+    const uint32_t upb = a.upb;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        if (t0 + j < nt) J.pre[t0 + j] = run;
+        const uint32_t t = t0 + j;
+        if (t < nt) {
+            J.pre[t] = run;
+            const uint64_t b = t / upb;
+            if (t % upb == 0 && b < J.nblocks) {
+                const uint64_t next = run + c[j] + (upb == 2 && j + 1 < 4 ? c[j + 1] : 0u);
+                J.lv.R[b] = (uint32_t)run;
+                if ((b & kBlocksPerSpanMask) == 0) J.lv.Hy[b >> (kSpanShift - 9)] = run;
+                for (uint64_t k2 = ceil_div(run, kSample); k2 * kSample < next; k2++) J.lv.S1[k2] = (uint32_t)b;
+                const uint64_t p0 = b * 512, p1 = min(p0 + 512, J.n);
+                for (uint64_t k2 = ceil_div(p0 - run, kSample); k2 * kSample < p1 - next; k2++)
+                    J.lv.S0[k2] = (uint32_t)b;
+            }
+        }
         run += c[j];
     }
-    if (t0 < nt && nt <= t0 + 4) J.pre[nt] = run;  // the total, read with the last tile's prefixes
+    if (t0 < nt && nt <= t0 + 4) {  // the total, read with the last tile's prefixes
+        J.pre[nt] = run;
+        J.lv.R[J.nblocks] = (uint32_t)run;
+        J.lv.Hy[J.nspans] = run;
+        *J.ones_out = run;
+    }
 }
 
 // ------------------------------------------------------------------ pass
 
 // One input stage: a tile, its sequence, its prefix, and its symbols.
 struct __align__(16) LwStage {
-    uint64_t pre[kLwPreCopy];  // pre[c] for the tile's chunks c and the next tile's first (one copy)
+    uint64_t pre[kLwMaxUnits + 2];  // pre[u] of the tile's units u and the next tile's first (one copy)
     LevelJob J;
     uint32_t tile;             // kNoTile: this CTA has no more tiles
     uint32_t full;             // a whole tile, 16-byte aligned: its symbols came in by bulk copy
@@ -370,8 +404,8 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
         S.tile = tile;
         S.full = full;
         fence_proxy_async_smem();
-        mbar_arrive_expect(&sh.bar[s], kLwPreCopy * 8 + (full ? kLwTileBytes : 0));
-        bulk_copy(S.pre, S.J.pre + (size_t)tile * kLwChunks, kLwPreCopy * 8, &sh.bar[s]);
+        mbar_arrive_expect(&sh.bar[s], Cfg::kPreCopy * 8 + (full ? kLwTileBytes : 0));
+        bulk_copy(S.pre, S.J.pre + (size_t)tile * Cfg::kUnits, Cfg::kPreCopy * 8, &sh.bar[s]);
         if (full)
             bulk_copy(in + s * kLwTileBytes, static_cast<const Sym *>(S.J.cur) + base, kLwTileBytes, &sh.bar[s]);
     }
@@ -388,10 +422,10 @@ struct LwOut {
     uint32_t offz, B1;       // their places in the split copy
 };
 
-// One tile: count, directory and placement into the shared copies, which
-// the caller sends out with lw_store after its next barrier (all threads).
-// Each warp works from the prefix of its own chunk, so no counts are
-// exchanged between the warps.  kWhole: the tile holds kTile symbols (no
+// One tile: count and placement into the shared copies, which the caller
+// sends out with lw_store after its next barrier (all threads).  Each warp
+// works from the prefix of its own range, so no counts are exchanged
+// between the warps.  kWhole: the tile holds kTile symbols (no
 // bound checks per symbol).
 template <typename Sym, bool kWhole>
 __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, const unsigned char *buf,
@@ -399,17 +433,15 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     using Cfg = LwCfg<Sym>;
     constexpr int kSps = Cfg::kSps;
     constexpr int kW = Cfg::kW;
-    constexpr uint32_t kWarpSyms = kLwWarpBytes / kW;
-    constexpr uint32_t kBlockBytes = 512 * kW;  // a rank block of the bitmap, in bytes of P_l
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t l = a.l;
     const LevelJob &J = S.J;
     const uint32_t tile = S.tile;
     const uint64_t base = (uint64_t)tile * Cfg::kTile;
     const uint32_t cnt = kWhole ? Cfg::kTile : (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
-    const uint64_t P = S.pre[0];                                 // ones before the tile
-    const uint32_t wx = (uint32_t)(S.pre[warp] - P);             // ones before this warp's range
-    const uint32_t tile_ones = (uint32_t)(S.pre[kLwChunks] - P);
+    const uint64_t P = S.pre[0];                                             // ones before the tile
+    const uint32_t wx = (uint32_t)(S.pre[warp * Cfg::kUnitsPerWarp] - P);    // before this warp's range
+    const uint32_t tile_ones = (uint32_t)(S.pre[Cfg::kUnits] - P);
     const uint32_t Zt = cnt - tile_ones;
     const uint32_t bsh = J.L - 1 - l;     // the level-l bit
     const bool has_next = J.nxt != nullptr;
@@ -440,63 +472,6 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
         }
     }
 
-    // Directory of this warp's range (lane 0): R and Hy at the rank blocks
-    // that start in it, the select samples whose one (zero) lies in it (the
-    // sample's block is the last one starting at or before it), and after
-    // the last tile the level totals.
-    if (lane == 0) {
-        const uint64_t block0 = base >> 9;
-        const uint32_t wsym0 = warp * kWarpSyms;
-        const uint32_t wv = cnt > wsym0 ? min(cnt - wsym0, kWarpSyms) : 0u;  // symbols in the range
-        uint32_t c[kLwSteps], wones = 0;
-#pragma unroll
-        for (int st = 0; st < kLwSteps; st++) {
-            c[st] = (tpk >> (16 * st)) & 0xffffu;
-            wones += c[st];
-        }
-        uint32_t run = 0;
-#pragma unroll
-        for (int st = 0; st < kLwSteps; st++) {
-            const uint32_t q = warp * kLwWarpBytes + st * 512;
-            const uint64_t block = block0 + q / kBlockBytes;
-            if (q % kBlockBytes == 0 && block < J.nblocks) {
-                const uint64_t v = P + wx + run;
-                J.lv.R[block] = (uint32_t)v;
-                if ((block & kBlocksPerSpanMask) == 0) J.lv.Hy[block >> (kSpanShift - 9)] = v;
-            }
-            run += c[st];
-        }
-        for (uint64_t k2 = ceil_div(P + wx, kSample); k2 * kSample < P + wx + wones; k2++) {
-            const uint32_t r = (uint32_t)(k2 * kSample - P);  // ones of the tile before the sample's one
-            uint32_t b = wsym0 / 512, o = wx;
-#pragma unroll
-            for (int st = 0; st < kLwSteps; st++) {
-                const uint32_t q = warp * kLwWarpBytes + st * 512;
-                if (st > 0 && q % kBlockBytes == 0 && o <= r) b = q / kBlockBytes;
-                o += c[st];
-            }
-            J.lv.S1[k2] = (uint32_t)(block0 + b);
-        }
-        const uint64_t zp = base - P;           // zeros before the tile
-        const uint32_t zw = wsym0 - wx;         // zeros of the tile before this warp's range
-        for (uint64_t k2 = ceil_div(zp + zw, kSample); k2 * kSample < zp + zw + (wv - wones); k2++) {
-            const uint32_t r = (uint32_t)(k2 * kSample - zp);
-            uint32_t b = wsym0 / 512, o = wx;
-#pragma unroll
-            for (int st = 0; st < kLwSteps; st++) {
-                const uint32_t q = warp * kLwWarpBytes + st * 512;
-                if (st > 0 && q % kBlockBytes == 0 && q / kW - o <= r) b = q / kBlockBytes;
-                o += c[st];
-            }
-            J.lv.S0[k2] = (uint32_t)(block0 + b);
-        }
-        if (tid == 0 && tile == J.ntiles - 1) {
-            const uint64_t total = P + tile_ones;
-            J.lv.R[J.nblocks] = (uint32_t)total;
-            J.lv.Hy[J.nspans] = total;
-            *J.ones_out = total;
-        }
-    }
     // What leaves after the barrier (read now: the stage record is
     // reused by the next claim).
     unsigned char *const bm_dst = reinterpret_cast<unsigned char *>(J.lv.words) + base / 8;
@@ -682,6 +657,8 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
 }
 
 constexpr size_t kLwSmem = kLwStages * kLwTileBytes + 2 * kLwSplitBytes + 2 * kLwBitsBytes + sizeof(LwShared);
+// Four CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA.
+static_assert(4 * (kLwSmem + 1024) <= 228 * 1024, "level pass shared memory");
 
 template <typename Sym>
 static cudaError_t launch_lw(const LevelLaunch &a, cudaStream_t st) {
@@ -743,7 +720,9 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.njobs = njobs;
     a.total_tiles = total_tiles;
     a.l = l;
-    a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * kLwChunks, kScanSeg);
+    a.units = lw_units((uint32_t)width);
+    a.upb = width == 4 ? 2u : 1u;  // units per rank block: 512 symbols
+    a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * a.units, kScanSeg);
     a.err = err;
     switch (width) {
         case 1: return launch_lw<uint8_t>(a, st);
