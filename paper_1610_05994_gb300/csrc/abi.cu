@@ -59,6 +59,18 @@ void dev_free(const Allocator &A, void *p, size_t bytes, cudaStream_t st) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Algorithmic bytes of one level step of n symbols of w bytes: the count
+// pass reads the symbols and writes level l's bitmap, or (from_bits) reads
+// that bitmap; it zeroes level l + 1's bitmap when the pass will write it;
+// the scan writes the directory (n/128); the pass reads P_l, writes P_{l+1}
+// and (next_bits) level l + 1's bitmap.
+double level_step_bytes(uint64_t n, int w, bool from_bits, bool pass, bool next_bits) {
+    const double nw = (double)n * w, bm = n / 8.0;
+    double b = (from_bits ? bm : nw + bm) + n / 128.0;
+    if (pass) b += 2 * nw + (next_bits ? 2 * bm : 0.0);
+    return b;
+}
+
 // ---------------------------------------------------------------- profiler
 // While enabled, every kernel launch of the library is bracketed by two CUDA
 // events on its own stream and tagged with the launch's algorithmic bytes
@@ -333,13 +345,17 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
         }
         const void *cur = S;
         void *bufs[2] = {b.ping, b.pong};
+        const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
+        bool from_bits = false;  // level l's bitmap was written by the pass of level l - 1
         for (uint32_t l = 0; l < t->L; l++) {
             void *nxt = (l + 1 < t->L) ? bufs[l & 1] : nullptr;
-            // read P_l, write the bitmap (n/8) and its directory (n/128), scatter P_{l+1}
-            const double bytes = nw + t->n / 8.0 + t->n / 128.0 + (nxt ? nw : 0.0);
-            ProfScope p(K_LEVEL_PASS, bytes, st);
+            const bool next_bits =
+                nxt && pass_writes_next_bits(level_boundaries(t->n, t->sigma, l), ntiles, t->width);
+            ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, from_bits, nxt != nullptr, next_bits), st);
             WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
-                                    &t->d_desc->lv[l].ones, b.cnt, b.pre, t->d_err, b.job_slot, st));
+                                    &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
+                                    next_bits ? t->h_desc.lv[l + 1].words : nullptr, t->d_err, b.job_slot, st));
+            from_bits = next_bits;
             cur = nxt;
         }
     }
@@ -611,6 +627,9 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         std::vector<uint32_t> seqs;
         size_t jobs_off, ts_off;  // in the staging tables
         uint32_t total, max_tiles;
+        bool from_bits;           // level l's bitmaps were written by the passes of level l - 1
+        bool next_bits;           // this level's pass writes level l + 1's bitmaps
+        bool do_pass;             // some sequence has a level l + 1
     };
     std::vector<LaunchPlan> plans;
     for (int c = 0; c < 3; c++)
@@ -723,11 +742,25 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
     }
     hts[count] = hist_tiles;
     sls[count] = hist_slabs;
+    bool prev_next_bits[3] = {false, false, false};
     for (auto &P : plans) {
         LevelJob *pj = reinterpret_cast<LevelJob *>(ht + P.jobs_off);
         uint32_t *pts = reinterpret_cast<uint32_t *>(ht + P.ts_off);
         uint32_t tiles = 0;
         P.max_tiles = 0;
+        // Whether this level's pass writes the next level's bitmaps: few
+        // tiles of the sequences that go on span a node boundary.
+        uint64_t bnd = 0, ptiles = 0;
+        P.do_pass = false;
+        for (uint32_t k : P.seqs)
+            if (L[k] > P.l + 1) {
+                P.do_pass = true;
+                bnd += level_boundaries(n[k], sigma[k], P.l);
+                ptiles += ceil_div(n[k], lw_tile_elems(width[k]));
+            }
+        P.next_bits = P.do_pass && pass_writes_next_bits(bnd, ptiles, P.width);
+        P.from_bits = P.l > 0 && prev_next_bits[wclass(P.width)];
+        prev_next_bits[wclass(P.width)] = P.next_bits;
         for (size_t q = 0; q < P.seqs.size(); q++) {
             const uint32_t k = P.seqs[q];
             const uint32_t l = P.l;
@@ -737,7 +770,8 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
             pj[q] = make_level_job(cur, nxt, n[k], width[k], L[k], l, reinterpret_cast<uint64_t *>(sc + so[k].ob),
                                    reinterpret_cast<uint64_t *>(sc + so[k].ze), hdesc[k].lv[l],
                                    &d_descs[k].lv[l].ones, reinterpret_cast<uint32_t *>(sc + so[k].cnt),
-                                   reinterpret_cast<uint64_t *>(sc + so[k].pre));
+                                   reinterpret_cast<uint64_t *>(sc + so[k].pre),
+                                   P.next_bits && l + 1 < L[k] ? hdesc[k].lv[l + 1].words : nullptr);
             pts[q] = tiles;
             tiles += (uint32_t)ntk;
             P.max_tiles = std::max(P.max_tiles, (uint32_t)ntk);
@@ -788,14 +822,12 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         for (size_t q = 0; q < plans.size(); q++) {
             const LaunchPlan &P = plans[q];
             double bytes = 0;
-            for (uint32_t k : P.seqs) {
-                const double nw = (double)n[k] * width[k];
-                bytes += nw + n[k] / 8.0 + n[k] / 128.0 + (P.l + 1 < L[k] ? nw : 0.0);
-            }
+            for (uint32_t k : P.seqs)
+                bytes += level_step_bytes(n[k], width[k], P.from_bits, P.l + 1 < L[k], P.next_bits && P.l + 1 < L[k]);
             ProfScope p(K_LEVEL_PASS, bytes, st);
             ck(launch_level_jobs(P.width, P.l, reinterpret_cast<const LevelJob *>(dt + P.jobs_off),
                                  reinterpret_cast<const uint32_t *>(dt + P.ts_off), (uint32_t)P.seqs.size(), P.total,
-                                 P.max_tiles, B->d_err, st));
+                                 P.max_tiles, P.from_bits, P.do_pass, B->d_err, st));
         }
     }
     if (use_graph) {
@@ -1181,7 +1213,8 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
     uint32_t herr = 0;
     if (cudaMemsetAsync(mem, 0, zeroed, st) != cudaSuccess ||
         launch_node_tables(Hex, L, ob, ze, st) != cudaSuccess ||
-        launch_level_pass(cur, (l + 1 < L) ? nxt : nullptr, n, sym_width, L, l, ob, ze, lv, ones, cnt, pre, err,
+        launch_level_pass(cur, (l + 1 < L) ? nxt : nullptr, n, sym_width, L, l, ob, ze, lv, ones, cnt, pre, false,
+                          nullptr, err,
                           job_slot, st) != cudaSuccess ||
         cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
         cudaGetLastError();

@@ -56,8 +56,10 @@ constexpr int kLwWarps = kLwThreads / 32;
 constexpr int kLwSteps = 2;                                        // 512-byte warp steps per warp
 constexpr uint32_t kLwWarpBytes = 512 * kLwSteps;                  // a warp's range of the tile
 constexpr uint32_t kLwTileBytes = kLwWarpBytes * kLwWarps;         // 8 KB
-constexpr uint32_t kLwSplitBytes = kLwTileBytes + 64;              // two runs + alignment slack
-constexpr uint32_t kLwBitsBytes = kLwTileBytes / 8;                // the bitmap copy (for bytes)
+// Two runs, each starting at its destination's offset in a 32-symbol word
+// of the next bitmap, plus the reads of whole 32-symbol groups (4-byte
+// symbols: 2048 + 124 symbols at most).
+constexpr uint32_t kLwSplitBytes = kLwTileBytes + 512;
 constexpr int kLwStages = 4;
 constexpr uint32_t kNoTile = 0xffffffffu;
 // The counts and prefixes are kept per unit of P_l: a warp's range or a rank
@@ -185,17 +187,25 @@ __device__ __forceinline__ void store_run(uintptr_t g0, uint32_t len, const unsi
 
 // ---------------------------------------------------------------- counts
 
-// The level-l ones of every unit of P_l: symbols with bit L - 1 - l set.
-// One warp per tile (kUnits units), the warps of the grid striding over the tiles together
-// (a window of consecutive tiles in flight, eight 16-byte loads per lane);
-// each warp finds a tile's job by binary search from its previous one.
+// The level-l ones of every unit of P_l.  One warp per tile (kUnits units),
+// the warps of the grid striding over the tiles together; each warp finds a
+// tile's job by binary search from its previous one.  Two kinds:
+//   kFromBits = false: read the symbols of P_l (eight 16-byte loads per lane
+//     in flight), count the symbols with bit L - 1 - l set, and write those
+//     bits as level l's bitmap;
+//   kFromBits = true: level l's bitmap was written by the pass of level
+//     l - 1; popcount it (n/8 bytes instead of n w).
+// Both zero the tile's range of level l + 1's bitmap when this level's pass
+// will write it (J.next_words), which the pass's boundary words need.
 constexpr int kCountThreads = 256;
 constexpr int kCountWarps = kCountThreads / 32;
 
-template <typename Sym>
-__global__ void __launch_bounds__(kCountThreads) count_kernel(LevelLaunch a) {
+template <typename Sym, bool kFromBits>
+__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(LevelLaunch a) {
     using Cfg = LwCfg<Sym>;
-    constexpr int kVecs = (int)(kLwTileBytes / 512);  // 16-byte loads per lane per tile
+    constexpr uint32_t kU = Cfg::kUnits;
+    constexpr uint32_t kUnitSyms = Cfg::kTile / kU;
+    constexpr uint32_t kTileWords = Cfg::kTile / 32;  // bitmap words of a tile
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kCountWarps;
     const uint32_t bsh_l = 1 + a.l;
@@ -213,35 +223,76 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(LevelLaunch a) {
             k = lo;
         }
         const LevelJob &J = a.jobs[k];
-        const Sym *S = static_cast<const Sym *>(J.cur);
         const uint32_t tile = g - a.tile_start[k];
         const uint64_t base = (uint64_t)tile * Cfg::kTile;
-        const uint32_t cnt = (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
-        const uint32_t bsh = J.L - bsh_l;
-        constexpr uint32_t kU = Cfg::kUnits;
-        constexpr int kPerUnit = kVecs / (int)kU;  // 16-byte loads per lane per unit
-        constexpr uint32_t kUnitSyms = Cfg::kTile / kU;
+        const uint64_t w0 = base / 32;            // the tile's first bitmap word
+        const uint64_t nwords = J.nblocks * 16;   // bitmap words of the level
         uint32_t c[kU];
 #pragma unroll
         for (int j = 0; j < (int)kU; j++) c[j] = 0;
-        if (cnt == Cfg::kTile && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
-            const uint4 *v = reinterpret_cast<const uint4 *>(S + base) + lane;
+        if (kFromBits) {
+            constexpr uint32_t kWU = kUnitSyms / 32;  // words per unit
+            const uint32_t *words = J.lv.words;
+            constexpr int kRows = (int)(kTileWords / 32), kSub = (int)(32 / kWU);
+            const uint32_t mysub = (uint32_t)lane / kWU;
 #pragma unroll
-            for (int h = 0; h < kVecs; h += 8) {
-                uint4 w[8];
+            for (int r = 0; r < kRows; r++) {
+                const uint64_t w = w0 + (uint32_t)r * 32 + lane;
+                const uint32_t pc = w < nwords ? __popc(__ldcs(words + w)) : 0u;
 #pragma unroll
-                for (int r = 0; r < 8; r++) w[r] = __ldcs(v + (h + r) * 32);
-#pragma unroll
-                for (int r = 0; r < 8; r++) {
-                    const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
-                    c[(h + r) / kPerUnit] += __popc(chunk_bits<Sym>(x, bsh));
-                }
+                for (int sub = 0; sub < kSub; sub++) c[r * kSub + sub] += mysub == (uint32_t)sub ? pc : 0u;
             }
         } else {
+            constexpr int kVecs = (int)(kLwTileBytes / 512);  // 16-byte loads per lane per tile
+            constexpr int kPerUnit = kVecs / (int)kU;
+            const Sym *S = static_cast<const Sym *>(J.cur);
+            const uint32_t cnt = (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
+            const uint32_t bsh = J.L - bsh_l;
+            unsigned char *bm = reinterpret_cast<unsigned char *>(J.lv.words);
+            if (cnt == Cfg::kTile && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
+                const uint4 *v = reinterpret_cast<const uint4 *>(S + base) + lane;
 #pragma unroll
-            for (int j = 0; j < (int)kU; j++)
-                for (uint32_t p = j * kUnitSyms + lane; p < min(cnt, (j + 1) * kUnitSyms); p += 32)
-                    c[j] += ((uint32_t)S[base + p] >> bsh) & 1u;
+                for (int h = 0; h < kVecs; h += 8) {
+                    uint4 w[8];
+#pragma unroll
+                    for (int r = 0; r < 8; r++) w[r] = __ldcs(v + (h + r) * 32);
+#pragma unroll
+                    for (int r = 0; r < 8; r++) {
+                        const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
+                        const uint32_t hb = chunk_bits<Sym>(x, bsh);
+                        c[(h + r) / kPerUnit] += __popc(hb);
+                        // The chunk's bits: 16 (8, 4) consecutive bits of the bitmap.
+                        const uint64_t bit0 = base + ((uint32_t)(h + r) * 512 + 16 * lane) / sizeof(Sym);
+                        if (sizeof(Sym) == 1) *reinterpret_cast<uint16_t *>(bm + bit0 / 8) = (uint16_t)hb;
+                        if (sizeof(Sym) == 2) bm[bit0 / 8] = (unsigned char)hb;
+                        if (sizeof(Sym) == 4) {
+                            const uint32_t nb = __shfl_down_sync(0xffffffffu, hb, 1);
+                            if ((lane & 1) == 0) bm[bit0 / 8] = (unsigned char)(hb | (nb << 4));
+                        }
+                    }
+                }
+            } else {
+                uint32_t *words = J.lv.words;
+#pragma unroll
+                for (int j = 0; j < (int)kU; j++)
+                    for (uint32_t p0 = j * kUnitSyms; p0 < (j + 1) * kUnitSyms; p0 += 32) {
+                        const uint32_t p = p0 + lane;
+                        const uint32_t bit = p < cnt ? ((uint32_t)S[base + p] >> bsh) & 1u : 0u;
+                        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+                        c[j] += bit;
+                        if (lane == 0 && w0 + p0 / 32 < nwords) words[w0 + p0 / 32] = bal;
+                    }
+            }
+        }
+        if (J.next_words) {
+            // Zero level l + 1's bitmap over the same positions (16-byte stores).
+            constexpr uint32_t kVec4 = kTileWords / 4;
+            uint4 *nw = reinterpret_cast<uint4 *>(J.next_words + w0);
+#pragma unroll
+            for (uint32_t r = 0; r < (kVec4 + 31) / 32; r++) {
+                const uint32_t i = r * 32 + lane;
+                if (i < kVec4 && w0 + 4ull * i < nwords) nw[i] = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
         uint32_t mine = 0;  // lane j < kU stores unit j's count
 #pragma unroll
@@ -359,6 +410,7 @@ struct __align__(16) LwStage {
     LevelJob J;
     uint32_t tile;             // kNoTile: this CTA has no more tiles
     uint32_t full;             // a whole tile, 16-byte aligned: its symbols came in by bulk copy
+    uint32_t skip;             // the job's last level: nothing to place
 };
 
 struct LwShared {
@@ -400,9 +452,11 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
     if (lane == 0) {
         const uint32_t tile = g - a.tile_start[k];
         const uint64_t base = (uint64_t)tile * Cfg::kTile;
-        const bool full = S.J.n - base >= Cfg::kTile && (reinterpret_cast<uintptr_t>(S.J.cur) & 15) == 0;
+        const bool skip = S.J.nxt == nullptr;
+        const bool full = !skip && S.J.n - base >= Cfg::kTile && (reinterpret_cast<uintptr_t>(S.J.cur) & 15) == 0;
         S.tile = tile;
         S.full = full;
+        S.skip = skip;
         fence_proxy_async_smem();
         mbar_arrive_expect(&sh.bar[s], Cfg::kPreCopy * 8 + (full ? kLwTileBytes : 0));
         bulk_copy(S.pre, S.J.pre + (size_t)tile * Cfg::kUnits, Cfg::kPreCopy * 8, &sh.bar[s]);
@@ -412,24 +466,28 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
 }
 
 // What a tile sends out by bulk store once every thread has written the
-// shared copies.
+// split copy: for a one-node tile its two runs.
 struct LwOut {
-    unsigned char *bm_dst;
-    uint32_t bm_bytes;
     bool runs;               // one node: a zeros run and a ones run
     uintptr_t gz_b, go_b;    // their destinations
-    uint32_t zlen, olen;     // their bytes
-    uint32_t offz, B1;       // their places in the split copy
+    uint32_t zt, ones;       // their symbols
+    uint32_t offz, B1;       // their places in the split copy (bytes)
+    uint64_t gz, go;         // their first positions in P_{l+1}
+    uint32_t *next_words;    // level l + 1's bitmap, when this pass writes it
+    uint32_t bsh_next;       // level l + 1's bit
 };
 
-// One tile: count and placement into the shared copies, which the caller
-// sends out with lw_store after its next barrier (all threads).  Each warp
-// works from the prefix of its own range, so no counts are exchanged
-// between the warps.  kWhole: the tile holds kTile symbols (no
-// bound checks per symbol).
+// One tile: count and placement into the split copy, which the caller sends
+// out with lw_store after its next barrier (all threads).  Each warp works
+// from the prefix of its own range, so no counts are exchanged between the
+// warps.  Level l's bitmap is already written (by the count pass or by the
+// pass of level l - 1); when J.next_words is set, this pass writes level
+// l + 1's: one-node tiles through lw_next_bits (the caller, after its
+// barrier, from the split copy), multi-node tiles bit by bit here.
+// kWhole: the tile holds kTile symbols (no bound checks per symbol).
 template <typename Sym, bool kWhole>
 __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, const unsigned char *buf,
-                                        unsigned char *split, unsigned char *bits, bool &bad, LwOut &out) {
+                                        unsigned char *split, bool &bad, LwOut &out) {
     using Cfg = LwCfg<Sym>;
     constexpr int kSps = Cfg::kSps;
     constexpr int kW = Cfg::kW;
@@ -444,7 +502,7 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     const uint32_t tile_ones = (uint32_t)(S.pre[Cfg::kUnits] - P);
     const uint32_t Zt = cnt - tile_ones;
     const uint32_t bsh = J.L - 1 - l;     // the level-l bit
-    const bool has_next = J.nxt != nullptr;
+    uint32_t *const next_words = J.next_words;
 
     // Count: level bits of the lane's chunks, per-lane and per-warp ones.
     uint32_t x[kLwSteps][4], h[kLwSteps];
@@ -460,122 +518,152 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     uint32_t tpk;
     const uint32_t lpk = warp_excl_scan(cpk, lane, tpk);
 
-    // The bitmap copy.
-#pragma unroll
-    for (int st = 0; st < kLwSteps; st++) {
-        const uint32_t ci = (warp * kLwWarpBytes + st * 512 + 16 * lane) / 16;  // chunk index
-        if (kSps == 16) reinterpret_cast<uint16_t *>(bits)[ci] = (uint16_t)h[st];
-        if (kSps == 8) bits[ci] = (unsigned char)h[st];
-        if (kSps == 4) {
-            const uint32_t nb = __shfl_down_sync(0xffffffffu, h[st], 1);
-            if ((lane & 1) == 0) bits[ci >> 1] = (unsigned char)(h[st] | (nb << 4));
-        }
-    }
-
-    // What leaves after the barrier (read now: the stage record is
-    // reused by the next claim).
-    unsigned char *const bm_dst = reinterpret_cast<unsigned char *>(J.lv.words) + base / 8;
-    const uint32_t bm_bytes = (uint32_t)(min((uint64_t)Cfg::kTile, J.nblocks * 512 - base) / 8);
-
     // Placement.
     bool runs = false;
     uintptr_t gz_b = 0, go_b = 0;
     uint32_t offz = 0, B1 = 0;
-    if (has_next) {
-        const uint32_t shv = J.L - l;  // key_l = s >> shv
-        const uint32_t nodes = 1u << l;
-        const Sym *sb = reinterpret_cast<const Sym *>(buf);
-        const uint32_t kfirst = (uint32_t)sb[0] >> shv, klast = (uint32_t)sb[cnt - 1] >> shv;
-        Sym *nxt = static_cast<Sym *>(J.nxt);
-        if (kfirst == klast && kfirst < nodes) {
-            const uint64_t gz = (base - P) + __ldg(J.ob + kfirst);  // first zero's position in P_{l+1}
-            const uint64_t go = P + __ldg(J.ze + kfirst);           // first one's position
-            if (gz + Zt > J.n || go + tile_ones > J.n) {
-                bad = true;
-            } else {
-                runs = true;
-                gz_b = reinterpret_cast<uintptr_t>(nxt + gz);
-                go_b = reinterpret_cast<uintptr_t>(nxt + go);
-                offz = (uint32_t)(gz_b & 15);
-                B1 = ((offz + Zt * kW + 15) & ~15u) + (uint32_t)(go_b & 15);
-                uint32_t stx = 0;  // ones of earlier steps of this warp
+    uint64_t gz = 0, go = 0;
+    const uint32_t shv = J.L - l;  // key_l = s >> shv
+    const uint32_t nodes = 1u << l;
+    const Sym *sb = reinterpret_cast<const Sym *>(buf);
+    const uint32_t kfirst = (uint32_t)sb[0] >> shv, klast = (uint32_t)sb[cnt - 1] >> shv;
+    Sym *nxt = static_cast<Sym *>(J.nxt);
+    if (kfirst == klast && kfirst < nodes) {
+        gz = (base - P) + __ldg(J.ob + kfirst);  // first zero's position in P_{l+1}
+        go = P + __ldg(J.ze + kfirst);           // first one's position
+        if (gz + Zt > J.n || go + tile_ones > J.n) {
+            bad = true;
+        } else {
+            runs = true;
+            gz_b = reinterpret_cast<uintptr_t>(nxt + gz);
+            go_b = reinterpret_cast<uintptr_t>(nxt + go);
+            // Each run starts at its destination's offset within a 32-symbol
+            // word of the next bitmap (which also agrees with the
+            // destination modulo 16 bytes, as the bulk stores need).
+            offz = (uint32_t)(gz & 31) * kW;
+            B1 = ((offz + Zt * kW + 32 * kW - 1) / (32 * kW)) * (32 * kW) + (uint32_t)(go & 31) * kW;
+            uint32_t stx = 0;  // ones of earlier steps of this warp
 #pragma unroll
-                for (int st = 0; st < kLwSteps; st++) {
-                    const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;
-                    const uint32_t o = wx + stx + ((lpk >> (16 * st)) & 0xffffu);  // ones before the chunk
-                    stx += (tpk >> (16 * st)) & 0xffffu;
-                    // A one goes to po; a zero to C + k kW - po (its zeros-before, scaled).
-                    uint32_t po = B1 + o * kW;
-                    const uint32_t C = offz + B1 + q;
+            for (int st = 0; st < kLwSteps; st++) {
+                const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;
+                const uint32_t o = wx + stx + ((lpk >> (16 * st)) & 0xffffu);  // ones before the chunk
+                stx += (tpk >> (16 * st)) & 0xffffu;
+                // A one goes to po; a zero to C + k kW - po (its zeros-before, scaled).
+                uint32_t po = B1 + o * kW;
+                const uint32_t C = offz + B1 + q;
 #pragma unroll
-                    for (int kk = 0; kk < kSps; kk++) {
-                        if (kWhole || q / kW + kk < cnt) {
-                            const bool one = (h[st] >> kk) & 1u;
-                            const uint32_t at = one ? po : C + kk * kW - po;
-                            const uint32_t sv = sym_at<Sym>(x[st], kk);
-                            if (kW == 1) split[at] = (unsigned char)sv;
-                            if (kW == 2) *reinterpret_cast<uint16_t *>(split + at) = (uint16_t)sv;
-                            if (kW == 4) *reinterpret_cast<uint32_t *>(split + at) = sv;
-                            po += one ? kW : 0;
-                        }
+                for (int kk = 0; kk < kSps; kk++) {
+                    if (kWhole || q / kW + kk < cnt) {
+                        const bool one = (h[st] >> kk) & 1u;
+                        const uint32_t at = one ? po : C + kk * kW - po;
+                        const uint32_t sv = sym_at<Sym>(x[st], kk);
+                        if (kW == 1) split[at] = (unsigned char)sv;
+                        if (kW == 2) *reinterpret_cast<uint16_t *>(split + at) = (uint16_t)sv;
+                        if (kW == 4) *reinterpret_cast<uint32_t *>(split + at) = sv;
+                        po += one ? kW : 0;
                     }
                 }
             }
-        } else {
-            // Several nodes: each symbol to its own position (Proposition 1).
-            // A warp takes 32 consecutive symbols of its range per round, so
-            // one store instruction covers runs of consecutive destinations
-            // and the node tables are read once per node; the ones before a
-            // symbol come from a ballot over the round.
-            constexpr uint32_t kWarpSyms = kLwWarpBytes / kW;
-            const uint32_t lt = (1u << lane) - 1u;
-            uint32_t o = wx;  // ones of the tile before this round
+        }
+    } else {
+        // Several nodes: each symbol to its own position (Proposition 1).
+        // A warp takes 32 consecutive symbols of its range per round, so
+        // one store instruction covers runs of consecutive destinations
+        // and the node tables are read once per node; the ones before a
+        // symbol come from a ballot over the round.  Level l + 1's bit of
+        // a symbol goes to its destination's bitmap word by atomicOr (these
+        // tiles are few wherever the pass writes level l + 1's bitmap).
+        constexpr uint32_t kWarpSyms = kLwWarpBytes / kW;
+        const uint32_t lt = (1u << lane) - 1u;
+        uint32_t o = wx;  // ones of the tile before this round
 #pragma unroll 4
-            for (uint32_t g = 0; g < kWarpSyms; g += 32) {
-                const uint32_t p = warp * kWarpSyms + g + lane;  // tile position
-                const bool in = kWhole || p < cnt;
-                const uint32_t sv = in ? (uint32_t)sb[p] : 0u;
-                const uint32_t bit = (sv >> bsh) & 1u;
-                const uint32_t bal = __ballot_sync(0xffffffffu, in && bit);
-                const uint32_t ob = o + __popc(bal & lt);  // ones of the tile before p
-                o += __popc(bal);
-                if (in) {
-                    const uint32_t v = sv >> shv;
-                    if (v >= nodes) {
-                        bad = true;
+        for (uint32_t g = 0; g < kWarpSyms; g += 32) {
+            const uint32_t p = warp * kWarpSyms + g + lane;  // tile position
+            const bool in = kWhole || p < cnt;
+            const uint32_t sv = in ? (uint32_t)sb[p] : 0u;
+            const uint32_t bit = (sv >> bsh) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, in && bit);
+            const uint32_t ob = o + __popc(bal & lt);  // ones of the tile before p
+            o += __popc(bal);
+            if (in) {
+                const uint32_t v = sv >> shv;
+                if (v >= nodes) {
+                    bad = true;
+                } else {
+                    const uint64_t dst = bit ? P + ob + __ldg(J.ze + v) : (base + p - P - ob) + __ldg(J.ob + v);
+                    if (dst < J.n) {
+                        nxt[dst] = (Sym)sv;
+                        if (next_words && ((sv >> (bsh - 1)) & 1u)) atomicOr(next_words + (dst >> 5), 1u << (dst & 31));
                     } else {
-                        const uint64_t dst = bit ? P + ob + __ldg(J.ze + v) : (base + p - P - ob) + __ldg(J.ob + v);
-                        if (dst < J.n)
-                            nxt[dst] = (Sym)sv;
-                        else
-                            bad = true;
+                        bad = true;
                     }
                 }
             }
         }
     }
-    fence_proxy_async_smem();  // the bitmap and split copies are read by bulk stores
-    out.bm_dst = bm_dst;
-    out.bm_bytes = bm_bytes;
+    fence_proxy_async_smem();  // the split copy is read by bulk stores
     out.runs = runs;
     out.gz_b = gz_b;
     out.go_b = go_b;
-    out.zlen = Zt * kW;
-    out.olen = tile_ones * kW;
+    out.zt = Zt;
+    out.ones = tile_ones;
     out.offz = offz;
     out.B1 = B1;
+    out.gz = gz;
+    out.go = go;
+    out.next_words = next_words;
+    out.bsh_next = bsh - 1;
 }
 
 // The bulk stores of a tile (threads 0..63, after the barrier that follows
-// lw_tile): the bitmap copy, and for a one-node tile its two runs.
-__device__ __forceinline__ void lw_store(const LwOut &o, const unsigned char *split, const unsigned char *bits) {
+// lw_tile): for a one-node tile its two runs.
+template <typename Sym>
+__device__ __forceinline__ void lw_store(const LwOut &o, const unsigned char *split) {
+    constexpr uint32_t kW = sizeof(Sym);
     const int tid = threadIdx.x;
-    if (tid == 32) bulk_store(o.bm_dst, bits, o.bm_bytes);
     if (o.runs) {
         if (tid < 32)
-            store_run(o.gz_b, o.zlen, split + o.offz, tid);
+            store_run(o.gz_b, o.zt * kW, split + o.offz, tid);
         else if (tid < 64)
-            store_run(o.go_b, o.olen, split + o.B1, tid - 32);
+            store_run(o.go_b, o.ones * kW, split + o.B1, tid - 32);
+    }
+}
+
+// Level l + 1's bitmap words of a one-node tile's two runs, from its split
+// copy (all threads, after the barrier that completes the copy).  A run
+// starts in the copy at its destination's offset within a 32-symbol word,
+// so bitmap word k of a run is the level l + 1 bits of the k-th group of 32
+// symbols there: a word inside the run is stored, a word shared with other
+// runs is ORed into the zeroed bitmap.
+template <typename Sym>
+__device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char *split) {
+    constexpr uint32_t kW = sizeof(Sym);
+    constexpr uint32_t kGroup = 32 * kW;  // bytes of 32 symbols
+    if (!o.runs || !o.next_words) return;
+    const uint32_t nwz = o.zt ? ((uint32_t)(o.gz & 31) + o.zt + 31) / 32 : 0u;
+    const uint32_t nwo = o.ones ? ((uint32_t)(o.go & 31) + o.ones + 31) / 32 : 0u;
+    const uint32_t zbase = 0, obase = o.B1 - (uint32_t)(o.go & 31) * kW;  // group 0 of each run
+    for (uint32_t t = threadIdx.x; t < nwz + nwo; t += kLwThreads) {
+        const bool zr = t < nwz;
+        const uint32_t k = zr ? t : t - nwz;
+        const unsigned char *g = split + (zr ? zbase : obase) + k * kGroup;
+        uint32_t bits = 0;
+#pragma unroll
+        for (uint32_t c = 0; c < kW * 2; c++) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(g + 16 * c);
+            const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+            bits |= chunk_bits<Sym>(x, o.bsh_next) << (c * (16 / kW));
+        }
+        const uint32_t first = (uint32_t)((zr ? o.gz : o.go) & 31);   // the run's first bit in word 0
+        const uint32_t len = zr ? o.zt : o.ones;
+        const uint32_t lo = k == 0 ? first : 0u;                      // bits of the run in word k
+        const uint32_t hi = min(32u, first + len - 32 * k);
+        const uint32_t mask = (hi == 32 ? ~0u : (1u << hi) - 1u) & ~((1u << lo) - 1u);
+        uint32_t *w = o.next_words + ((zr ? o.gz : o.go) >> 5) + k;
+        if (mask == ~0u)
+            *w = bits;
+        else if (bits & mask)
+            atomicOr(w, bits & mask);
     }
 }
 
@@ -585,8 +673,7 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *in = smem;                                  // kLwStages x kLwTileBytes
     unsigned char *split_base = in + kLwStages * kLwTileBytes;  // 2 x kLwSplitBytes
-    unsigned char *bits_base = split_base + 2 * kLwSplitBytes;  // 2 x kLwBitsBytes
-    LwShared &sh = *reinterpret_cast<LwShared *>(bits_base + 2 * kLwBitsBytes);
+    LwShared &sh = *reinterpret_cast<LwShared *>(split_base + 2 * kLwSplitBytes);
     const int tid = threadIdx.x;
 
     // This CTA's tiles: a contiguous range of the launch's global tiles.
@@ -607,8 +694,9 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
     __syncthreads();
 
     bool failed = false, bad = false;
-    // One barrier per tile: it publishes tile i's shared copies to the
-    // threads that bulk-store them and stage i + 1 to every thread.
+    // One barrier per tile: it publishes tile i's split copy to every thread
+    // (for the bulk stores and the next level's bitmap words) and stage
+    // i + 1 to every thread.
     if (__syncthreads_or(!mbar_wait(&sh.bar[0], 0u))) failed = true;
     for (uint32_t i = 0; !failed; i++) {
         const int s = (int)(i % kLwStages), par = (int)(i & 1);
@@ -619,28 +707,31 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
         if (tid < 32)
             lw_claim<Sym>(a, sh, in, (int)((i + kLwStages - 1) % kLwStages), g_begin + i + kLwStages - 1, g_end, k,
                           have_job);
-        const LevelJob &J = S.J;
         unsigned char *buf = in + s * kLwTileBytes;
         unsigned char *split = split_base + par * kLwSplitBytes;
-        unsigned char *bits = bits_base + par * kLwBitsBytes;
-        const uint32_t tile = S.tile;
-        const uint64_t base = (uint64_t)tile * Cfg::kTile;
-        const uint32_t cnt = (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
-        if (!S.full) {
-            // The sequence's last tile, or symbols not 16-byte aligned: plain
-            // loads, zero past the end.
-            const Sym *src = static_cast<const Sym *>(J.cur);
-            Sym *sb = reinterpret_cast<Sym *>(buf);
-            for (uint32_t p = tid; p < Cfg::kTile; p += kLwThreads) sb[p] = p < cnt ? src[base + p] : (Sym)0;
-            __syncthreads();
-        }
         LwOut out;
-        if (cnt == Cfg::kTile)
-            lw_tile<Sym, true>(a, S, buf, split, bits, bad, out);
-        else
-            lw_tile<Sym, false>(a, S, buf, split, bits, bad, out);
-        // The copies of the other parity (tile i - 1) are reused by tile
-        // i + 1: their bulk stores must have read them before the barrier.
+        out.runs = false;
+        if (!S.skip) {
+            const LevelJob &J = S.J;
+            const uint32_t tile = S.tile;
+            const uint64_t base = (uint64_t)tile * Cfg::kTile;
+            const uint32_t cnt = (uint32_t)min((uint64_t)Cfg::kTile, J.n - base);
+            if (!S.full) {
+                // The sequence's last tile, or symbols not 16-byte aligned:
+                // plain loads, zero past the end.
+                const Sym *src = static_cast<const Sym *>(J.cur);
+                Sym *sb = reinterpret_cast<Sym *>(buf);
+                for (uint32_t p = tid; p < Cfg::kTile; p += kLwThreads) sb[p] = p < cnt ? src[base + p] : (Sym)0;
+                __syncthreads();
+            }
+            if (cnt == Cfg::kTile)
+                lw_tile<Sym, true>(a, S, buf, split, bad, out);
+            else
+                lw_tile<Sym, false>(a, S, buf, split, bad, out);
+        }
+        // The split copy of the other parity (tile i - 1) is reused by tile
+        // i + 1: its bulk stores must have read it before the barrier (its
+        // bitmap words were read by every thread before this barrier).
         if (tid == 0 || tid == 32) bulk_wait_read0();
         const uint32_t i1 = i + 1;
         const bool ok = mbar_wait(&sh.bar[i1 % kLwStages], (i1 / kLwStages) & 1u);
@@ -648,20 +739,21 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
             failed = true;
             break;
         }
-        lw_store(out, split, bits);
+        lw_store<Sym>(out, split);
         if (tid == 0 || tid == 32) bulk_commit();
+        lw_next_bits<Sym>(out, split);
     }
     if (tid == 0 || tid == 32) bulk_wait_all();
     if (failed && tid == 0) atomicOr(a.err, kErrTimeout);
     if (bad) atomicOr(a.err, kErrTimeout);
 }
 
-constexpr size_t kLwSmem = kLwStages * kLwTileBytes + 2 * kLwSplitBytes + 2 * kLwBitsBytes + sizeof(LwShared);
+constexpr size_t kLwSmem = kLwStages * kLwTileBytes + 2 * kLwSplitBytes + sizeof(LwShared);
 // Four CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA.
 static_assert(4 * (kLwSmem + 1024) <= 228 * 1024, "level pass shared memory");
 
 template <typename Sym>
-static cudaError_t launch_lw(const LevelLaunch &a, cudaStream_t st) {
+static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass, cudaStream_t st) {
     // Persistent grid: every resident CTA slot, at most one CTA per tile.
     static int slots = 0, sms = 0;
     if (!slots) {
@@ -683,17 +775,24 @@ static cudaError_t launch_lw(const LevelLaunch &a, cudaStream_t st) {
     // Counts: a warp per tile, at most eight CTAs per SM.
     const uint32_t cw = (a.total_tiles + kCountWarps - 1) / kCountWarps;
     const uint32_t g0 = cw < (uint32_t)(sms * 8) ? cw : (uint32_t)(sms * 8);
-    count_kernel<Sym><<<g0, kCountThreads, 0, st>>>(a);
+    if (from_bits)
+        count_kernel<Sym, true><<<g0, kCountThreads, 0, st>>>(a);
+    else
+        count_kernel<Sym, false><<<g0, kCountThreads, 0, st>>>(a);
     scan_sums_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
     scan_segs_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
-    const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
-    level_pass_kernel<Sym><<<grid, kLwThreads, kLwSmem, st>>>(a);
-    note_launches(4);
+    note_launches(3);
+    if (do_pass) {
+        const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
+        level_pass_kernel<Sym><<<grid, kLwThreads, kLwSmem, st>>>(a);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 
 LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l, const uint64_t *ob,
-                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre) {
+                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre,
+                        uint32_t *next_words) {
     LevelJob j;
     j.cur = cur;
     j.nxt = (l + 1 < L) ? nxt : nullptr;
@@ -708,11 +807,13 @@ LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint3
     j.ze = ze + ((1ull << l) - 1);
     j.cnt = cnt;
     j.pre = pre;
+    j.next_words = (l + 1 < L) ? next_words : nullptr;
     return j;
 }
 
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
-                              uint32_t total_tiles, uint32_t max_job_tiles, uint32_t *err, cudaStream_t st) {
+                              uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
+                              uint32_t *err, cudaStream_t st) {
     if (njobs == 0 || total_tiles == 0) return cudaSuccess;
     LevelLaunch a;
     a.jobs = jobs;
@@ -725,9 +826,9 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * a.units, kScanSeg);
     a.err = err;
     switch (width) {
-        case 1: return launch_lw<uint8_t>(a, st);
-        case 2: return launch_lw<uint16_t>(a, st);
-        case 4: return launch_lw<uint32_t>(a, st);
+        case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, st);
+        case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, st);
+        case 4: return launch_lw<uint32_t>(a, from_bits, do_pass, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -746,16 +847,17 @@ size_t level_job_slot_bytes() { return (sizeof(LevelJob) + 2 * sizeof(uint32_t) 
 
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
-                              uint64_t *pre, uint32_t *err, void *job_slot, cudaStream_t st) {
+                              uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
+                              cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, cnt, pre);
+    const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, cnt, pre, next_words);
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
     uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
     put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, err, st);
+    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, from_bits, l + 1 < L, err, st);
 }
 
 }  // namespace wt

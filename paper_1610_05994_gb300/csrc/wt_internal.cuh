@@ -261,21 +261,45 @@ struct __align__(16) LevelJob {
     LevelDesc lv;              // its level-l arrays
     uint64_t *ones_out;
     const uint64_t *ob, *ze;   // its level-l node tables
-    uint32_t *cnt;             // ntiles: ones of each tile on level l
-    uint64_t *pre;             // lw_prefix_bytes: ones before each tile
+    uint32_t *cnt;             // lw_counts_bytes: ones of each unit on level l
+    uint64_t *pre;             // lw_prefix_bytes: ones before each unit
+    uint32_t *next_words;      // level l + 1's bitmap when this pass writes it, else nullptr
 };
 
 LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l, const uint64_t *ob,
-                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre);
+                        const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt, uint64_t *pre,
+                        uint32_t *next_words);
 size_t level_job_bytes();
-// Level l of every job (all of one width): counts, prefix scan, pass.
+// At most how many node boundaries P_l of one sequence has: level l has
+// 2^l nodes, at most sigma of them and at most n non-empty.
+inline uint64_t level_boundaries(uint64_t n, uint64_t sigma, uint32_t l) {
+    uint64_t m = l < 63 ? (1ull << l) : ~0ull;
+    if (sigma < m) m = sigma;
+    if (n < m) m = n;
+    return m ? m - 1 : 0;
+}
+// Whether the pass of level l writes level l + 1's bitmap (from its split
+// copies), so that level l + 1's count pass reads n/8 bytes instead of n w:
+// for 1- and 2-byte symbols (for 4-byte symbols the pass's extra reads of
+// its split copy cost as much as the count pass saves), and when at most one
+// tile in 64 spans a node boundary, so the tiles placed symbol by symbol
+// (whose bits go out one atomicOr each) are few.  Otherwise level l + 1's
+// count pass writes the bitmap from the symbols.
+inline bool pass_writes_next_bits(uint64_t boundaries, uint64_t tiles, int width) {
+    return width <= 2 && boundaries * 64 < tiles;
+}
+// Level l of every job (all of one width): counts (from the symbols, which
+// also writes level l's bitmap, or from_bits: from that bitmap), prefix
+// scan with the rank directory, and (do_pass) the pass that places P_{l+1}.
 // max_job_tiles: the most tiles of any one job.
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
-                              uint32_t total_tiles, uint32_t max_job_tiles, uint32_t *err, cudaStream_t st);
+                              uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
+                              uint32_t *err, cudaStream_t st);
 // One sequence (job_slot: level_job_slot_bytes() of device memory).
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
-                              uint64_t *pre, uint32_t *err, void *job_slot, cudaStream_t st);
+                              uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
+                              cudaStream_t st);
 
 // Kernel (d): dd-direct build of all levels for small sigma (dd.cu).
 struct DdScratch {
