@@ -190,7 +190,7 @@ __device__ __forceinline__ void store_run(uintptr_t g0, uint32_t len, const unsi
 // The level-l ones of every unit of P_l.  One warp per tile (kUnits units),
 // the warps of the grid striding over the tiles together; each warp finds a
 // tile's job by binary search from its previous one.  Two kinds:
-//   kFromBits = false: read the symbols of P_l (eight 16-byte loads per lane
+//   kFromBits = false: read the symbols of P_l (four 16-byte loads per lane
 //     in flight), count the symbols with bit L - 1 - l set, and write those
 //     bits as level l's bitmap;
 //   kFromBits = true: level l's bitmap was written by the pass of level
@@ -201,7 +201,7 @@ constexpr int kCountThreads = 256;
 constexpr int kCountWarps = kCountThreads / 32;
 
 template <typename Sym, bool kFromBits>
-__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(LevelLaunch a) {
+__global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) {
     using Cfg = LwCfg<Sym>;
     constexpr uint32_t kU = Cfg::kUnits;
     constexpr uint32_t kUnitSyms = Cfg::kTile / kU;
@@ -251,23 +251,25 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(LevelLaunch a) 
             unsigned char *bm = reinterpret_cast<unsigned char *>(J.lv.words);
             if (cnt == Cfg::kTile && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
                 const uint4 *v = reinterpret_cast<const uint4 *>(S + base) + lane;
+                // The lane's chunk of load r is 16 (8, 4) consecutive bits of
+                // the bitmap, at byte (base + (512 r + 16 lane) / w) / 8.
+                unsigned char *bl = bm + base / 8 + (16 * lane / sizeof(Sym)) / 8;
 #pragma unroll
-                for (int h = 0; h < kVecs; h += 8) {
-                    uint4 w[8];
+                for (int h = 0; h < kVecs; h += 4) {
+                    uint4 w[4];
 #pragma unroll
-                    for (int r = 0; r < 8; r++) w[r] = __ldcs(v + (h + r) * 32);
+                    for (int r = 0; r < 4; r++) w[r] = __ldcs(v + (h + r) * 32);
 #pragma unroll
-                    for (int r = 0; r < 8; r++) {
+                    for (int r = 0; r < 4; r++) {
                         const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
                         const uint32_t hb = chunk_bits<Sym>(x, bsh);
                         c[(h + r) / kPerUnit] += __popc(hb);
-                        // The chunk's bits: 16 (8, 4) consecutive bits of the bitmap.
-                        const uint64_t bit0 = base + ((uint32_t)(h + r) * 512 + 16 * lane) / sizeof(Sym);
-                        if (sizeof(Sym) == 1) *reinterpret_cast<uint16_t *>(bm + bit0 / 8) = (uint16_t)hb;
-                        if (sizeof(Sym) == 2) bm[bit0 / 8] = (unsigned char)hb;
+                        unsigned char *d = bl + (h + r) * (512 / sizeof(Sym) / 8);
+                        if (sizeof(Sym) == 1) *reinterpret_cast<uint16_t *>(d) = (uint16_t)hb;
+                        if (sizeof(Sym) == 2) *d = (unsigned char)hb;
                         if (sizeof(Sym) == 4) {
                             const uint32_t nb = __shfl_down_sync(0xffffffffu, hb, 1);
-                            if ((lane & 1) == 0) bm[bit0 / 8] = (unsigned char)(hb | (nb << 4));
+                            if ((lane & 1) == 0) *d = (unsigned char)(hb | (nb << 4));
                         }
                     }
                 }
