@@ -59,16 +59,16 @@ void dev_free(const Allocator &A, void *p, size_t bytes, cudaStream_t st) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Algorithmic bytes of one level step of n symbols of w bytes: the count
-// pass reads the symbols and writes level l's bitmap, or (from_bits) reads
-// that bitmap; it zeroes level l + 1's bitmap when the pass will write it;
-// the scan writes the directory (n/128); the pass reads P_l, writes P_{l+1}
-// and (next_bits) level l + 1's bitmap.
-double level_step_bytes(uint64_t n, int w, bool from_bits, bool pass, bool next_bits) {
-    const double nw = (double)n * w, bm = n / 8.0;
-    double b = (from_bits ? bm : nw + bm) + n / 128.0;
-    if (pass) b += 2 * nw + (next_bits ? 2 * bm : 0.0);
-    return b;
+// Algorithmic bytes of one level step of n symbols of w bytes, the byte
+// model of the level-wise method: read P_l (n w), write level l's bitmap
+// (n/8) and its directory (n/128), write P_{l+1} (n w) on every level but
+// the last.  (What the kernels move beyond it, such as the count pass's
+// read, shows in the measured DRAM traffic; where the pass of level l - 1
+// hands level l its bitmap, the count pass reads n/8 instead of n w and
+// the last level needs no pass, so fewer bytes than the model move.)
+double level_step_bytes(uint64_t n, int w, bool has_next) {
+    const double nw = (double)n * w;
+    return nw + n / 8.0 + n / 128.0 + (has_next ? nw : 0.0);
 }
 
 // ---------------------------------------------------------------- profiler
@@ -351,7 +351,7 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
             void *nxt = (l + 1 < t->L) ? bufs[l & 1] : nullptr;
             const bool next_bits =
                 nxt && pass_writes_next_bits(level_boundaries(t->n, t->sigma, l), ntiles, t->width);
-            ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, from_bits, nxt != nullptr, next_bits), st);
+            ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, nxt != nullptr), st);
             WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
                                     &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
                                     next_bits ? t->h_desc.lv[l + 1].words : nullptr, t->d_err, b.job_slot, st));
@@ -823,7 +823,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
             const LaunchPlan &P = plans[q];
             double bytes = 0;
             for (uint32_t k : P.seqs)
-                bytes += level_step_bytes(n[k], width[k], P.from_bits, P.l + 1 < L[k], P.next_bits && P.l + 1 < L[k]);
+                bytes += level_step_bytes(n[k], width[k], P.l + 1 < L[k]);
             ProfScope p(K_LEVEL_PASS, bytes, st);
             ck(launch_level_jobs(P.width, P.l, reinterpret_cast<const LevelJob *>(dt + P.jobs_off),
                                  reinterpret_cast<const uint32_t *>(dt + P.ts_off), (uint32_t)P.seqs.size(), P.total,
