@@ -42,13 +42,27 @@ __global__ void __launch_bounds__(kHistThreads) hist_shared_kernel(const Sym *__
     const bool vec = (reinterpret_cast<uintptr_t>(S) & 15) == 0;
     const uint64_t nvec = vec ? n / kPer : 0;
     const uint4 *V = reinterpret_cast<const uint4 *>(S);
-    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < nvec;
-         k += (uint64_t)gridDim.x * blockDim.x) {
-        uint4 q = __ldcs(V + k);
-        const Sym *e = reinterpret_cast<const Sym *>(&q);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    auto add_vec = [&](const uint4 q) {
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int t = 0; t < kPer; t++) hist_add_shared<Sym>(mine, sigma, (uint32_t)e[t], bad);
+        for (int t = 0; t < kPer; t++) {
+            const uint32_t v = sizeof(Sym) == 4 ? w[t] : (w[t / (4 / sizeof(Sym))] >> (8 * sizeof(Sym) * (t % (4 / sizeof(Sym))))) &
+                                                              (sizeof(Sym) == 1 ? 0xffu : 0xffffu);
+            hist_add_shared<Sym>(mine, sigma, v, bad);
+        }
+    };
+    uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    // Four vectors in flight per thread.
+    for (; k + 3 * stride < nvec; k += 4 * stride) {
+        const uint4 q0 = __ldcs(V + k), q1 = __ldcs(V + k + stride), q2 = __ldcs(V + k + 2 * stride),
+                    q3 = __ldcs(V + k + 3 * stride);
+        add_vec(q0);
+        add_vec(q1);
+        add_vec(q2);
+        add_vec(q3);
     }
+    for (; k < nvec; k += stride) add_vec(__ldcs(V + k));
     for (uint64_t k = nvec * kPer + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
          k += (uint64_t)gridDim.x * blockDim.x)
         hist_add_shared<Sym>(mine, sigma, (uint32_t)S[k], bad);
@@ -58,6 +72,75 @@ __global__ void __launch_bounds__(kHistThreads) hist_shared_kernel(const Sym *__
         uint32_t sum = 0;
         for (uint32_t k = 0; k < copies; k++) sum += bins[k * sigma + c];
         if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&hist[c]), (unsigned long long)sum);
+    }
+}
+
+// Alphabets of at most four byte codes (DNA-like): no bins at all.  The two
+// low bit planes of four bytes give, by three popcounts, how many of them
+// are 1, 2 and 3; the rest are 0.  Any higher bit is a symbol out of range.
+// Per-thread counts, one warp sum and four 64-bit atomics per warp.
+__global__ void __launch_bounds__(kHistThreads, 2) hist_tiny_kernel(const uint8_t *__restrict__ S, uint64_t n,
+                                                                 uint32_t sigma, uint64_t *__restrict__ hist,
+                                                                 uint32_t *__restrict__ err) {
+    uint32_t c1 = 0, c2 = 0, c3 = 0, total = 0, high = 0;
+    auto add_word = [&](uint32_t x) {
+        high |= x & 0xfcfcfcfcu;
+        const uint32_t lo = x & 0x01010101u, hi = (x >> 1) & 0x01010101u;
+        const uint32_t n3 = __popc(lo & hi);
+        c3 += n3;
+        c1 += __popc(lo) - n3;
+        c2 += __popc(hi) - n3;
+    };
+    const bool vec = (reinterpret_cast<uintptr_t>(S) & 15) == 0;
+    const uint64_t nvec = vec ? n / 16 : 0;
+    const uint4 *V = reinterpret_cast<const uint4 *>(S);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (; k + 3 * stride < nvec; k += 4 * stride) {
+        const uint4 q[4] = {__ldcs(V + k), __ldcs(V + k + stride), __ldcs(V + k + 2 * stride),
+                            __ldcs(V + k + 3 * stride)};
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            add_word(q[r].x);
+            add_word(q[r].y);
+            add_word(q[r].z);
+            add_word(q[r].w);
+        }
+        total += 64;
+    }
+    for (; k < nvec; k += stride) {
+        const uint4 q = __ldcs(V + k);
+        add_word(q.x);
+        add_word(q.y);
+        add_word(q.z);
+        add_word(q.w);
+        total += 16;
+    }
+    for (uint64_t j = nvec * 16 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += stride) {
+        const uint32_t s = S[j];
+        high |= s & ~3u;
+        c1 += s == 1;
+        c2 += s == 2;
+        c3 += s == 3;
+        total += 1;
+    }
+    c1 = __reduce_add_sync(0xffffffffu, c1);
+    c2 = __reduce_add_sync(0xffffffffu, c2);
+    c3 = __reduce_add_sync(0xffffffffu, c3);
+    total = __reduce_add_sync(0xffffffffu, total);
+    high = __reduce_or_sync(0xffffffffu, high);
+    if ((threadIdx.x & 31) == 0) {
+        const uint32_t c[4] = {total - c1 - c2 - c3, c1, c2, c3};
+        bool bad = high != 0;
+#pragma unroll
+        for (uint32_t v = 0; v < 4; v++) {
+            if (v < sigma) {
+                if (c[v]) atomicAdd(reinterpret_cast<unsigned long long *>(&hist[v]), (unsigned long long)c[v]);
+            } else if (c[v]) {
+                bad = true;
+            }
+        }
+        if (bad) atomicOr(err, kErrSymbol);
     }
 }
 
@@ -174,7 +257,13 @@ static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64
     grid = grid > ceil_div(n, per_cta_cap) ? grid : ceil_div(n, per_cta_cap);
     uint64_t want = ceil_div(n, (uint64_t)kHistThreads * 16);
     if (grid > want) grid = want ? want : 1;
-    if (sigma <= kHistSmemBins) {
+    if (sizeof(Sym) == 1 && sigma <= 4) {
+        // Two resident CTAs per SM (52 registers a thread), all of them at once.
+        const uint64_t g2 = grid < (uint64_t)sm_count() * 2 ? grid : (uint64_t)sm_count() * 2;
+        hist_tiny_kernel<<<(unsigned)g2, kHistThreads, 0, st>>>(reinterpret_cast<const uint8_t *>(S), n,
+                                                                (uint32_t)sigma, hist, err);
+        note_launches(1);
+    } else if (sigma <= kHistSmemBins) {
         uint32_t sig = (uint32_t)sigma;
         uint32_t copies = (uint32_t)(kHistSmemBins / sigma);
         const uint32_t warps = kHistThreads / 32;
