@@ -61,6 +61,7 @@ constexpr uint32_t kLwTileBytes = kLwWarpBytes * kLwWarps;         // 8 KB
 // symbols: 2048 + 124 symbols at most).
 constexpr uint32_t kLwSplitBytes = kLwTileBytes + 512;
 constexpr int kLwStages = 4;
+constexpr uint32_t kLwStageBits = kLwTileBytes / 8;                 // a stage's copy of the level's bitmap (bytes)
 constexpr uint32_t kNoTile = 0xffffffffu;
 // The counts and prefixes are kept per unit of P_l: a warp's range or a rank
 // block of the bitmap, whichever is shorter (kLwWarpBytes or 512 symbols).
@@ -413,6 +414,7 @@ struct __align__(16) LwStage {
     uint32_t tile;             // kNoTile: this CTA has no more tiles
     uint32_t full;             // a whole tile, 16-byte aligned: its symbols came in by bulk copy
     uint32_t skip;             // the job's last level: nothing to place
+    uint32_t bits_bytes;       // bytes of level l's bitmap copied for the tile
 };
 
 struct LwShared {
@@ -460,10 +462,18 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
         S.full = full;
         S.skip = skip;
         fence_proxy_async_smem();
-        mbar_arrive_expect(&sh.bar[s], Cfg::kPreCopy * 8 + (full ? kLwTileBytes : 0));
+        // Level l's bitmap over the tile (written by the count pass or by
+        // the pass of level l - 1), clamped to the bitmap's 512-bit blocks.
+        const uint32_t bits_bytes =
+            skip ? 0u : (uint32_t)min((uint64_t)(Cfg::kTile / 8), S.J.nblocks * 64 - base / 8);
+        S.bits_bytes = bits_bytes;
+        mbar_arrive_expect(&sh.bar[s], Cfg::kPreCopy * 8 + (full ? kLwTileBytes : 0) + bits_bytes);
         bulk_copy(S.pre, S.J.pre + (size_t)tile * Cfg::kUnits, Cfg::kPreCopy * 8, &sh.bar[s]);
         if (full)
             bulk_copy(in + s * kLwTileBytes, static_cast<const Sym *>(S.J.cur) + base, kLwTileBytes, &sh.bar[s]);
+        if (bits_bytes)
+            bulk_copy(in + kLwStages * kLwTileBytes + s * kLwStageBits,
+                      reinterpret_cast<const unsigned char *>(S.J.lv.words) + base / 8, bits_bytes, &sh.bar[s]);
     }
 }
 
@@ -489,7 +499,7 @@ struct LwOut {
 // kWhole: the tile holds kTile symbols (no bound checks per symbol).
 template <typename Sym, bool kWhole>
 __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, const unsigned char *buf,
-                                        unsigned char *split, bool &bad, LwOut &out) {
+                                        const unsigned char *sbits, unsigned char *split, bool &bad, LwOut &out) {
     using Cfg = LwCfg<Sym>;
     constexpr int kSps = Cfg::kSps;
     constexpr int kW = Cfg::kW;
@@ -506,7 +516,8 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     const uint32_t bsh = J.L - 1 - l;     // the level-l bit
     uint32_t *const next_words = J.next_words;
 
-    // Count: level bits of the lane's chunks, per-lane and per-warp ones.
+    // Count: level bits of the lane's chunks (16, 8 or 4 consecutive bits of
+    // the level's bitmap, copied into the stage), per-lane and per-warp ones.
     uint32_t x[kLwSteps][4], h[kLwSteps];
     uint32_t cpk = 0;  // step st's count in bits [16 st, 16 st + 16)
 #pragma unroll
@@ -514,7 +525,14 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
         const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;  // the chunk's byte in the tile
         const uint4 v = *reinterpret_cast<const uint4 *>(buf + q);
         x[st][0] = v.x, x[st][1] = v.y, x[st][2] = v.z, x[st][3] = v.w;
-        h[st] = chunk_bits<Sym>(x[st], bsh);
+        const uint32_t b0 = q / kW / 8;  // the chunk's first bitmap byte in the tile
+        uint32_t hb = 0;
+        if (kWhole || b0 < S.bits_bytes) {
+            if (kSps == 16) hb = *reinterpret_cast<const uint16_t *>(sbits + b0);
+            if (kSps == 8) hb = sbits[b0];
+            if (kSps == 4) hb = (sbits[b0] >> (4 * (lane & 1))) & 15u;
+        }
+        h[st] = hb;
         cpk += (uint32_t)__popc(h[st]) << (16 * st);
     }
     uint32_t tpk;
@@ -673,8 +691,8 @@ template <typename Sym>
 __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_kernel(LevelLaunch a) {
     using Cfg = LwCfg<Sym>;
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *in = smem;                                  // kLwStages x kLwTileBytes
-    unsigned char *split_base = in + kLwStages * kLwTileBytes;  // 2 x kLwSplitBytes
+    unsigned char *in = smem;  // kLwStages x kLwTileBytes of symbols, then kLwStages x kLwStageBits of bitmap
+    unsigned char *split_base = in + kLwStages * (kLwTileBytes + kLwStageBits);  // 2 x kLwSplitBytes
     LwShared &sh = *reinterpret_cast<LwShared *>(split_base + 2 * kLwSplitBytes);
     const int tid = threadIdx.x;
 
@@ -726,10 +744,11 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
                 for (uint32_t p = tid; p < Cfg::kTile; p += kLwThreads) sb[p] = p < cnt ? src[base + p] : (Sym)0;
                 __syncthreads();
             }
+            const unsigned char *sbits = in + kLwStages * kLwTileBytes + s * kLwStageBits;
             if (cnt == Cfg::kTile)
-                lw_tile<Sym, true>(a, S, buf, split, bad, out);
+                lw_tile<Sym, true>(a, S, buf, sbits, split, bad, out);
             else
-                lw_tile<Sym, false>(a, S, buf, split, bad, out);
+                lw_tile<Sym, false>(a, S, buf, sbits, split, bad, out);
         }
         // The split copy of the other parity (tile i - 1) is reused by tile
         // i + 1: its bulk stores must have read it before the barrier (its
@@ -750,7 +769,7 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
     if (bad) atomicOr(a.err, kErrTimeout);
 }
 
-constexpr size_t kLwSmem = kLwStages * kLwTileBytes + 2 * kLwSplitBytes + sizeof(LwShared);
+constexpr size_t kLwSmem = kLwStages * (kLwTileBytes + kLwStageBits) + 2 * kLwSplitBytes + sizeof(LwShared);
 // Four CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA.
 static_assert(4 * (kLwSmem + 1024) <= 228 * 1024, "level pass shared memory");
 
