@@ -175,3 +175,25 @@ def test_mid_alphabet_histogram(sigma, dtype, n):
     want[sigma + 1:] = n
     assert np.array_equal(starts, want)
     compare_tree(t, S, sigma, check_dir=n < (1 << 24))
+
+
+@pytest.mark.parametrize("sigma", [(1 << 20) + 3, 100_000, (1 << 22)])
+def test_large_alphabets_at_millions_of_symbols(sigma):
+    """Four-byte codes over large alphabets (the replicated global histogram,
+    deep levels of tiny nodes) at n > 2^22: whole trees equal the oracle's."""
+    W = wt()
+    n = (1 << 22) + 12345
+    S = inputs.zipf(n, sigma, 1.2, 4242, np.uint32)
+    t = W.Tree.build(to_dev(S), sigma)
+    compare_tree(t, S, sigma)
+    t.free()
+
+
+def test_large_alphabet_flags_out_of_range_symbols():
+    W = wt()
+    sigma = (1 << 20) + 3
+    S = inputs.zipf((1 << 22) + 7, sigma, 1.2, 99, np.uint32)
+    S[123457] = sigma
+    with pytest.raises(W.WTError) as e:
+        W.Tree.build(to_dev(S), sigma)
+    assert e.value.status == W.ERR_SYMBOL_RANGE
