@@ -90,7 +90,11 @@ wt_handle wt_build(const void *S, uint64_t n, uint64_t sigma, int sym_width);
  * valid immediately for further calls on the same stream.  Arguments are
  * checked on the host; device-side faults (symbol range, timeout) are
  * reported by wt_wait.  S must stay valid until the build completes.
- * variant is a wt_variant.
+ * variant is a wt_variant.  Host symbols are copied to the device first: with
+ * the default allocator and a stream that is not being captured, the copy
+ * runs on a library-owned stream of the device and `stream` waits for it, so
+ * the copy of one call overlaps the builds enqueued before it; otherwise the
+ * copy is enqueued on `stream`.
  */
 wt_handle wt_build_async(const void *S, uint64_t n, uint64_t sigma, int sym_width, int variant,
                          void *stream);

@@ -875,6 +875,24 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
     return WT_OK;
 }
 
+// The library's host-to-device copy stream of the current device (created
+// once, non-blocking).
+cudaStream_t copy_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
 wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int variant, cudaStream_t st) {
     wt_status r = check_args(S, n, sigma, width);
     if (r != WT_OK) {
@@ -908,12 +926,28 @@ wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int 
     void *staged = nullptr;
     const size_t sbytes = n * (uint64_t)width;
     if (r == WT_OK && n > 0 && !is_device_pointer(S)) {
-        staged = dev_alloc(t->alloc, sbytes, st);
-        if (!staged)
+        // Host symbols are staged on the library's copy stream when the
+        // default allocator is in use and st is not being captured: the copy
+        // for one call then overlaps the build of the previous call on st,
+        // and st waits only for its own copy.  Otherwise the copy goes on st.
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cudaGetLastError();
+        cudaStream_t cs = (!t->alloc.alloc && cap == cudaStreamCaptureStatusNone) ? copy_stream() : nullptr;
+        cudaStream_t on = cs ? cs : st;
+        staged = dev_alloc(t->alloc, sbytes, on);
+        if (!staged) {
             r = WT_ERR_OOM;
-        else if (cudaMemcpyAsync(staged, S, sbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        } else if (cudaMemcpyAsync(staged, S, sbytes, cudaMemcpyHostToDevice, on) != cudaSuccess) {
             cudaGetLastError();
             r = WT_ERR_CUDA;
+        } else if (cs) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(ev, cs) != cudaSuccess || cudaStreamWaitEvent(st, ev, 0) != cudaSuccess) {
+                cudaGetLastError();
+                r = WT_ERR_CUDA;
+            }
+            if (ev) cudaEventDestroy(ev);
         }
         Sd = staged;
     }
