@@ -321,13 +321,23 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
     const BuildScratch &b = sc.b;
     const double nw = (double)t->n * t->width;
     const uint32_t R = hist_replicas(t->n, t->sigma);
+    const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
+    // Level 0's count pass rides on the histogram's read of S where it can
+    // (1-byte symbols): level 0's bitmap and unit counts, and level 1's
+    // bitmap zeroed when level 0's pass will write it.
+    const bool fuse0 = !R && t->L > 0 && level0_fusable(S, t->n, t->width, t->sigma);
+    const bool next0 = t->L > 1 && pass_writes_next_bits(level_boundaries(t->n, t->sigma, 0), ntiles, t->width);
     {
         ProfScope p(K_HIST, nw, st);
-        if (R)
+        if (R) {
             WT_CK(launch_histogram_replicated(S, t->n, t->width, t->sigma, reinterpret_cast<uint32_t *>(b.hist), R,
                                               t->d_err, st));
-        else
+        } else if (fuse0) {
+            const Level0Fuse z{t->h_desc.lv[0].words, b.cnt, next0 ? t->h_desc.lv[1].words : nullptr, t->L - 1};
+            WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st, &z));
+        } else {
             WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st));
+        }
     }
     if (t->L > 0) {
         const double leaves = (double)(1ull << t->L);
@@ -345,7 +355,6 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
         }
         const void *cur = S;
         void *bufs[2] = {b.ping, b.pong};
-        const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
         bool from_bits = false;  // level l's bitmap was written by the pass of level l - 1
         for (uint32_t l = 0; l < t->L; l++) {
             void *nxt = (l + 1 < t->L) ? bufs[l & 1] : nullptr;
@@ -354,7 +363,8 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
             ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, nxt != nullptr), st);
             WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
                                     &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
-                                    next_bits ? t->h_desc.lv[l + 1].words : nullptr, t->d_err, b.job_slot, st));
+                                    next_bits ? t->h_desc.lv[l + 1].words : nullptr, t->d_err, b.job_slot, st,
+                                    l == 0 && fuse0));
             from_bits = next_bits;
             cur = nxt;
         }

@@ -25,13 +25,37 @@ __device__ __forceinline__ void hist_add_shared(uint32_t *bins, uint32_t sigma, 
         bad = true;
 }
 
+// The bits at shift bsh of the 16 bytes of q, packed: bit k = byte k (one
+// multiply gathers the four top bits of a word into a nibble).
+__device__ __forceinline__ uint32_t byte_bits16(const uint4 q, uint32_t bsh) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    uint32_t h = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) h |= ((((w[i] << (7 - bsh)) & 0x80808080u) * 0x00204081u) >> 28) << (4 * i);
+    return h;
+}
+
+// Level 0's count pass for vector k of S (16 symbols; the 32 lanes of a warp
+// hold the 32 vectors of one 512-symbol unit, all active together).
+__device__ __forceinline__ void level0_vector(const Level0Fuse &z, uint64_t k, const uint4 q) {
+    const uint32_t hb = byte_bits16(q, z.bsh);
+    reinterpret_cast<uint16_t *>(z.words)[k] = (uint16_t)hb;
+    if (z.next) reinterpret_cast<uint16_t *>(z.next)[k] = 0;
+    const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(hb));
+    if ((threadIdx.x & 31) == 0) z.cnt[k / 32] = c;
+}
+
+bool level0_fusable(const void *S, uint64_t n, int width, uint64_t sigma) {
+    return width == 1 && sigma >= 2 && n > 0 && n % 512 == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0;
+}
+
 // Shared-memory histogram: `copies` private copies of the sigma bins (warp w
 // uses copy w % copies) spread same-bin contention for small alphabets.
 template <typename Sym>
 __global__ void __launch_bounds__(kHistThreads) hist_shared_kernel(const Sym *__restrict__ S, uint64_t n,
                                                                    uint32_t sigma, uint32_t copies,
                                                                    uint64_t *__restrict__ hist,
-                                                                   uint32_t *__restrict__ err) {
+                                                                   uint32_t *__restrict__ err, Level0Fuse z) {
     extern __shared__ uint32_t bins[];
     const uint32_t total = sigma * copies;
     for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) bins[k] = 0;
@@ -53,6 +77,7 @@ __global__ void __launch_bounds__(kHistThreads) hist_shared_kernel(const Sym *__
         }
     };
     uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const bool fuse = sizeof(Sym) == 1 && z.words != nullptr;
     // Four vectors in flight per thread.
     for (; k + 3 * stride < nvec; k += 4 * stride) {
         const uint4 q0 = __ldcs(V + k), q1 = __ldcs(V + k + stride), q2 = __ldcs(V + k + 2 * stride),
@@ -61,8 +86,18 @@ __global__ void __launch_bounds__(kHistThreads) hist_shared_kernel(const Sym *__
         add_vec(q1);
         add_vec(q2);
         add_vec(q3);
+        if (fuse) {
+            level0_vector(z, k, q0);
+            level0_vector(z, k + stride, q1);
+            level0_vector(z, k + 2 * stride, q2);
+            level0_vector(z, k + 3 * stride, q3);
+        }
     }
-    for (; k < nvec; k += stride) add_vec(__ldcs(V + k));
+    for (; k < nvec; k += stride) {
+        const uint4 q = __ldcs(V + k);
+        add_vec(q);
+        if (fuse) level0_vector(z, k, q);
+    }
     for (uint64_t k = nvec * kPer + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
          k += (uint64_t)gridDim.x * blockDim.x)
         hist_add_shared<Sym>(mine, sigma, (uint32_t)S[k], bad);
@@ -80,8 +115,8 @@ __global__ void __launch_bounds__(kHistThreads) hist_shared_kernel(const Sym *__
 // are 1, 2 and 3; the rest are 0.  Any higher bit is a symbol out of range.
 // Per-thread counts, one warp sum and four 64-bit atomics per warp.
 __global__ void __launch_bounds__(kHistThreads, 2) hist_tiny_kernel(const uint8_t *__restrict__ S, uint64_t n,
-                                                                 uint32_t sigma, uint64_t *__restrict__ hist,
-                                                                 uint32_t *__restrict__ err) {
+                                                                    uint32_t sigma, uint64_t *__restrict__ hist,
+                                                                    uint32_t *__restrict__ err, Level0Fuse z) {
     uint32_t c1 = 0, c2 = 0, c3 = 0, total = 0, high = 0;
     auto add_word = [&](uint32_t x) {
         high |= x & 0xfcfcfcfcu;
@@ -96,6 +131,7 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_tiny_kernel(const uint8_
     const uint4 *V = reinterpret_cast<const uint4 *>(S);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const bool fuse = z.words != nullptr;
     for (; k + 3 * stride < nvec; k += 4 * stride) {
         const uint4 q[4] = {__ldcs(V + k), __ldcs(V + k + stride), __ldcs(V + k + 2 * stride),
                             __ldcs(V + k + 3 * stride)};
@@ -105,6 +141,7 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_tiny_kernel(const uint8_
             add_word(q[r].y);
             add_word(q[r].z);
             add_word(q[r].w);
+            if (fuse) level0_vector(z, k + r * stride, q[r]);
         }
         total += 64;
     }
@@ -114,6 +151,7 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_tiny_kernel(const uint8_
         add_word(q.y);
         add_word(q.z);
         add_word(q.w);
+        if (fuse) level0_vector(z, k, q);
         total += 16;
     }
     for (uint64_t j = nvec * 16 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += stride) {
@@ -249,7 +287,9 @@ static int sm_count() {
 
 template <typename Sym>
 static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64_t *hist, uint32_t *err,
-                               cudaStream_t st) {
+                               cudaStream_t st, const Level0Fuse *fuse) {
+    Level0Fuse z{};
+    if (fuse && sizeof(Sym) == 1 && level0_fusable(S, n, 1, sigma) && sigma <= kHistSmemBins) z = *fuse;
     if (n == 0) return cudaSuccess;
     const Sym *s = static_cast<const Sym *>(S);
     const uint64_t per_cta_cap = 1ull << 30;  // keeps every u32 shared bin below 2^32
@@ -261,7 +301,7 @@ static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64
         // Two resident CTAs per SM (52 registers a thread), all of them at once.
         const uint64_t g2 = grid < (uint64_t)sm_count() * 2 ? grid : (uint64_t)sm_count() * 2;
         hist_tiny_kernel<<<(unsigned)g2, kHistThreads, 0, st>>>(reinterpret_cast<const uint8_t *>(S), n,
-                                                                (uint32_t)sigma, hist, err);
+                                                                (uint32_t)sigma, hist, err, z);
         note_launches(1);
     } else if (sigma <= kHistSmemBins) {
         uint32_t sig = (uint32_t)sigma;
@@ -273,7 +313,7 @@ static cudaError_t histogram_t(const void *S, uint64_t n, uint64_t sigma, uint64
         cudaError_t e = cudaFuncSetAttribute(hist_shared_kernel<Sym>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        hist_shared_kernel<Sym><<<(unsigned)grid, kHistThreads, smem, st>>>(s, n, sig, copies, hist, err);
+        hist_shared_kernel<Sym><<<(unsigned)grid, kHistThreads, smem, st>>>(s, n, sig, copies, hist, err, z);
         note_launches(1);
     } else if (sigma <= kPackedMaxSigma) {
         const size_t smem = (kPackedMaxSigma / 2) * sizeof(uint32_t);
@@ -310,11 +350,11 @@ static cudaError_t histogram_rep_t(const void *S, uint64_t n, uint64_t sigma, ui
 }
 
 cudaError_t launch_histogram(const void *S, uint64_t n, int width, uint64_t sigma, uint64_t *hist, uint32_t *err,
-                             cudaStream_t st) {
+                             cudaStream_t st, const Level0Fuse *fuse) {
     switch (width) {
-        case 1: return histogram_t<uint8_t>(S, n, sigma, hist, err, st);
-        case 2: return histogram_t<uint16_t>(S, n, sigma, hist, err, st);
-        case 4: return histogram_t<uint32_t>(S, n, sigma, hist, err, st);
+        case 1: return histogram_t<uint8_t>(S, n, sigma, hist, err, st, fuse);
+        case 2: return histogram_t<uint16_t>(S, n, sigma, hist, err, st, nullptr);
+        case 4: return histogram_t<uint32_t>(S, n, sigma, hist, err, st, nullptr);
     }
     return cudaErrorInvalidValue;
 }

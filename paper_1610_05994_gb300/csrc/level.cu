@@ -774,7 +774,7 @@ constexpr size_t kLwSmem = kLwStages * (kLwTileBytes + kLwStageBits) + 2 * kLwSp
 static_assert(4 * (kLwSmem + 1024) <= 228 * 1024, "level pass shared memory");
 
 template <typename Sym>
-static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass, cudaStream_t st) {
+static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass, bool counted, cudaStream_t st) {
     // Persistent grid: every resident CTA slot, at most one CTA per tile.
     static int slots = 0, sms = 0;
     if (!slots) {
@@ -796,13 +796,16 @@ static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass,
     // Counts: a warp per tile, at most eight CTAs per SM.
     const uint32_t cw = (a.total_tiles + kCountWarps - 1) / kCountWarps;
     const uint32_t g0 = cw < (uint32_t)(sms * 8) ? cw : (uint32_t)(sms * 8);
-    if (from_bits)
-        count_kernel<Sym, true><<<g0, kCountThreads, 0, st>>>(a);
-    else
-        count_kernel<Sym, false><<<g0, kCountThreads, 0, st>>>(a);
+    if (!counted) {
+        if (from_bits)
+            count_kernel<Sym, true><<<g0, kCountThreads, 0, st>>>(a);
+        else
+            count_kernel<Sym, false><<<g0, kCountThreads, 0, st>>>(a);
+        note_launches(1);
+    }
     scan_sums_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
     scan_segs_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
-    note_launches(3);
+    note_launches(2);
     if (do_pass) {
         const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
         level_pass_kernel<Sym><<<grid, kLwThreads, kLwSmem, st>>>(a);
@@ -834,7 +837,7 @@ LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint3
 
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
                               uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
-                              uint32_t *err, cudaStream_t st) {
+                              uint32_t *err, cudaStream_t st, bool counted) {
     if (njobs == 0 || total_tiles == 0) return cudaSuccess;
     LevelLaunch a;
     a.jobs = jobs;
@@ -847,9 +850,9 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * a.units, kScanSeg);
     a.err = err;
     switch (width) {
-        case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, st);
-        case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, st);
-        case 4: return launch_lw<uint32_t>(a, from_bits, do_pass, st);
+        case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, counted, st);
+        case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, counted, st);
+        case 4: return launch_lw<uint32_t>(a, from_bits, do_pass, counted, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -869,7 +872,7 @@ size_t level_job_slot_bytes() { return (sizeof(LevelJob) + 2 * sizeof(uint32_t) 
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
                               uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool counted) {
     if (n == 0) return cudaSuccess;
     const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, cnt, pre, next_words);
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
@@ -878,7 +881,7 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, from_bits, l + 1 < L, err, st);
+    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, from_bits, l + 1 < L, err, st, counted);
 }
 
 }  // namespace wt

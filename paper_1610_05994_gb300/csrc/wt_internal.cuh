@@ -225,8 +225,18 @@ struct BuildScratch {
 
 // Kernel (a): histogram of S into hist (zeroed by the caller) and the symbol
 // range check; then the exclusive scan into hex.
+// Level 0's count pass folded into the histogram's read of S (1-byte
+// symbols, S 16-byte aligned, n a multiple of 512): the level-0 bit (bit
+// bsh) of every symbol goes to level 0's bitmap (words), the ones of every
+// 512-symbol unit to cnt (the count pass's layout), and level 1's bitmap is
+// zeroed (next, when level 0's pass writes it; else nullptr).
+struct Level0Fuse {
+    uint32_t *words, *cnt, *next;
+    uint32_t bsh;
+};
+bool level0_fusable(const void *S, uint64_t n, int width, uint64_t sigma);
 cudaError_t launch_histogram(const void *S, uint64_t n, int width, uint64_t sigma, uint64_t *hist,
-                             uint32_t *err, cudaStream_t st);
+                             uint32_t *err, cudaStream_t st, const Level0Fuse *fuse = nullptr);
 // Large alphabets with n < 2^32: hist_replicas(n, sigma) replicas (0 = use
 // launch_histogram instead) of sigma u32 counters, zeroed by the caller.
 uint32_t hist_replicas(uint64_t n, uint64_t sigma);
@@ -292,14 +302,16 @@ inline bool pass_writes_next_bits(uint64_t boundaries, uint64_t tiles, int width
 // also writes level l's bitmap, or from_bits: from that bitmap), prefix
 // scan with the rank directory, and (do_pass) the pass that places P_{l+1}.
 // max_job_tiles: the most tiles of any one job.
+// counted: the units' counts (and level l's bitmap) are already in place
+// (level 0 folded into the histogram): no count pass.
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
                               uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
-                              uint32_t *err, cudaStream_t st);
+                              uint32_t *err, cudaStream_t st, bool counted = false);
 // One sequence (job_slot: level_job_slot_bytes() of device memory).
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
                               uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
-                              cudaStream_t st);
+                              cudaStream_t st, bool counted = false);
 
 // Kernel (d): dd-direct build of all levels for small sigma (dd.cu).
 struct DdScratch {
