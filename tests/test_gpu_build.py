@@ -94,6 +94,19 @@ def test_symbol_out_of_range_is_reported():
     assert e.value.status == W.ERR_SYMBOL_RANGE
 
 
+@pytest.mark.parametrize("sigma,bad", [(3, 3), (4, 200), (96, 96)])
+@pytest.mark.parametrize("n", [1 << 16, (1 << 16) + 5])
+def test_symbol_out_of_range_in_long_byte_sequences(sigma, bad, n):
+    """The bit-plane histogram (sigma <= 4) and the histogram that also counts
+    level 0 (n a multiple of 512) flag a symbol >= sigma."""
+    W = wt()
+    S = inputs.uniform(n, sigma, 7, np.uint8)
+    S[n // 3] = bad
+    with pytest.raises(W.WTError) as e:
+        W.Tree.build(to_dev(S), sigma)
+    assert e.value.status == W.ERR_SYMBOL_RANGE
+
+
 def test_invalid_arguments():
     W = wt()
     S = to_dev(np.zeros(10, np.uint8))
