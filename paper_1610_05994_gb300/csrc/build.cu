@@ -3,8 +3,10 @@
 // (a)  histogram of the leaf codes + exclusive scan  -> Hex (node starts of
 //      every level at once: node v of level l starts at Hex[v << (L - l)]),
 //      replacing the per-level "count" and parPrefixSum steps of Algorithm 1.
+//      For 1-byte symbols the histogram's read of S also does level 0's
+//      count pass (level 0's bitmap and unit counts).
 // (a') per-level node tables OB / ZE from Hex.
-// The fused level pass (b + c) is in level.cu.
+// The level step (b + c) is in level.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

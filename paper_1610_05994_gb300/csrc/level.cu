@@ -1,47 +1,52 @@
-// level.cu -- kernels (b) + (c): the fused per-level pass of the level-wise
-// build, with its count pass and prefix scan.
+// level.cu -- kernels (b) + (c): the level step of the level-wise build
+// (count pass, prefix scan with the rank directory, and the fused pass).
 //
-// One pass over P_l (the symbols in level-l order) does, per tile of 8 KB:
-//   (b) packs the level-l bit of every symbol into the bitmap;
-//   (c) places every symbol at its position in P_{l+1}:
+// One pass over P_l (the symbols in level-l order) places, per tile of 8 KB,
+// every symbol at its position in P_{l+1}:
 //          bit 0:  dst = zeros_before(p) + OB_l[v]
 //          bit 1:  dst = ones_before(p)  + ZE_l[v]
-//       with v = key_l(s), OB_l[v] = ones on level l before node v's start and
-//       ZE_l[v] = zeros on level l up to node v's end.  This is the stable
-//       counting-sort placement of Algorithm 1 ("bitmapSetBit at C[node]++",
-//       Section 3.1) written as a closed form of two prefix counts, so one
-//       global scan serves every node of the level.
+// with v = key_l(s), OB_l[v] = ones on level l before node v's start and
+// ZE_l[v] = zeros on level l up to node v's end.  This is the stable
+// counting-sort placement of Algorithm 1 ("bitmapSetBit at C[node]++",
+// Section 3.1) written as a closed form of two prefix counts, so one global
+// scan serves every node of the level.
 //
-// Where the ones before a position come from: a count pass reads P_l at full
-// bandwidth and stores the level-l ones of every unit (a warp's 1 KB range of
-// a tile, or a 512-symbol rank block when that is shorter); a segmented scan
-// turns them into prefixes before the pass starts.  The same scan writes the
-// level's rank directory (R, Hy) and select samples (S1, S0), since the
-// prefix at a rank block's first unit is R itself.  So the tiles of a pass
-// are independent, and inside a tile every warp starts from its own prefix:
-// no CTA waits for another and no warp for the others' counts.  (Counting
-// the next level's ones inside the pass, where each symbol's destination is
-// known, cost more instructions than the extra read.)
+// Where the ones before a position come from: a count pass stores the
+// level-l ones of every unit (a warp's 1 KB range of a tile, or a 512-symbol
+// rank block when that is shorter); a segmented scan turns them into
+// prefixes before the pass starts.  The same scan writes the level's rank
+// directory (R, Hy) and select samples (S1, S0), since the prefix at a rank
+// block's first unit is R itself.  So the tiles of a pass are independent,
+// and inside a tile every warp starts from its own prefix: no CTA waits for
+// another and no warp for the others' counts.
 //
-// GPU structure: a persistent CTA of 256 threads takes a contiguous range of
-// tiles and keeps four stages: warp 0 claims a tile three ahead and one
-// thread issues TMA bulk copies (cp.async.bulk) of its symbols and of its
-// unit prefixes into a shared-memory stage while the CTA works on the
-// current one.  Per tile:
+// Where level l's bitmap comes from: for 1- and 2-byte symbols, on levels
+// with few node boundaries, the pass of level l - 1 writes it from its
+// shared split copy of P_l (every 32 consecutive symbols there are one
+// bitmap word), and the count pass only popcounts it; otherwise the count
+// pass writes it from the symbols.  The last level therefore needs no pass.
+//
+// GPU structure of the pass: a persistent CTA of 256 threads takes a
+// contiguous range of tiles and keeps four stages: warp 0 claims a tile
+// three ahead and one thread issues TMA bulk copies (cp.async.bulk) of its
+// symbols, its unit prefixes and its slice of level l's bitmap into a
+// shared-memory stage while the CTA works on the current one.  Per tile:
 //   * a lane owns 16 consecutive bytes of each 512-byte warp step, so its
-//     level bits are 16 (8, 4) consecutive bits of the bitmap: they go to a
-//     shared-memory copy of the tile's bitmap that leaves with one bulk
-//     store; per-lane counts of two steps share one shuffle scan;
+//     level bits are 16 (8, 4) consecutive bits of the bitmap copy; per-lane
+//     counts of two steps share one shuffle scan;
 //   * when the whole tile lies in one node (the common case: nodes are far
 //     larger than a tile except on the deepest levels of large alphabets),
 //     its zeros and ones go to two contiguous runs of P_{l+1}: each lane
 //     walks its symbols in order with one running pointer, writing every
-//     symbol into a shared-memory copy of the two runs laid out at the
-//     destination's 16-byte alignment; the aligned interior of each run
-//     leaves with one bulk store, the ragged ends with byte stores.  Tiles
-//     that span several nodes store every symbol at its own destination.
-//   * one CTA barrier per tile: it hands the tile's shared copies to the
-//     threads that bulk-store them and the next stage to every thread.
+//     symbol into a shared-memory split copy of the two runs laid out at the
+//     destination's offset within a 32-symbol bitmap word (which also agrees
+//     with the destination modulo 16 bytes); the aligned interior of each
+//     run leaves with one bulk store, the ragged ends with byte stores.
+//     Tiles that span several nodes store every symbol at its own
+//     destination.
+//   * one CTA barrier per tile: it hands the split copy to the threads that
+//     bulk-store it and write the next bitmap's words, and the next stage to
+//     every thread.
 // The only waits are on the bulk copies, bounded like every wait of the
 // library.
 #include <cuda_runtime.h>
