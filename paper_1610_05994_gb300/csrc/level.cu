@@ -27,8 +27,8 @@
 // pass writes it from the symbols.  The last level therefore needs no pass.
 //
 // GPU structure of the pass: a persistent CTA of 256 threads takes a
-// contiguous range of tiles and keeps four stages: warp 0 claims a tile
-// three ahead and one thread issues TMA bulk copies (cp.async.bulk) of its
+// contiguous range of tiles and keeps four stages: the last warp claims a
+// tile three ahead and one thread issues TMA bulk copies (cp.async.bulk) of its
 // symbols, its unit prefixes and its slice of level l's bitmap into a
 // shared-memory stage while the CTA works on the current one.  Per tile:
 //   * a lane owns 16 consecutive bytes of each 512-byte warp step, so its
@@ -428,7 +428,7 @@ struct LwShared {
     uint64_t bar[kLwStages];               // a stage is in place
 };
 
-// Claims this CTA's tile g into stage s (warp 0, all lanes): the stage
+// Claims this CTA's tile g into stage s (the claiming warp, all lanes): the stage
 // record (copied by the lanes) and, by bulk copy, the tile's chunk prefixes
 // and (whole aligned tiles) the symbols.  k and have_job are the same in every lane.
 template <typename Sym>
@@ -707,12 +707,15 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
     const uint32_t g_end = min(g_begin + per, a.total_tiles);
     uint32_t k = 0;  // the claimer's job index
     bool have_job = false;
+    // The last warp claims the stages (warps 0 and 1 issue the bulk stores),
+    // which spreads the per-tile extra work over three warps.
+    const bool claimer = (tid >> 5) == kLwWarps - 1;
     if (tid == 0) {
         for (int s = 0; s < kLwStages; s++) mbar_init(&sh.bar[s], 1);
         fence_mbar_init();
     }
-    __syncwarp();
-    if (tid < 32) {
+    __syncthreads();
+    if (claimer) {
         if (g_begin < g_end) k = find_job(a, g_begin);
         for (int s = 0; s < kLwStages - 1; s++) lw_claim<Sym>(a, sh, in, s, g_begin + s, g_end, k, have_job);
     }
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
         if (S.tile == kNoTile) break;  // every thread reads the same record
         // Stage (i + 3) % 4 held tile i - 1, which is done: claim tile i + 3
         // into it while the other warps count this one.
-        if (tid < 32)
+        if (claimer)
             lw_claim<Sym>(a, sh, in, (int)((i + kLwStages - 1) % kLwStages), g_begin + i + kLwStages - 1, g_end, k,
                           have_job);
         unsigned char *buf = in + s * kLwTileBytes;
