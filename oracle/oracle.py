@@ -57,8 +57,10 @@ def _load():
         lib.wto_level_symbol.argtypes = [vp, u64, i32, u64, u32, u64, vp]
         lib.wto_access_trace.argtypes = [vp, u64, u64, u64, vp, vp]
         lib.wto_node_starts.argtypes = [vp, u64, i32, u64, vp]
+        lib.wto_merge.argtypes = [vp, vp, vp, u32, u64, vp]
         for f in ("wto_level_order", "wto_build_bits", "wto_pwt", "wto_dd", "wto_directory",
-                  "wto_access", "wto_rank", "wto_select", "wto_level_symbol", "wto_access_trace", "wto_node_starts"):
+                  "wto_access", "wto_rank", "wto_select", "wto_level_symbol", "wto_access_trace", "wto_node_starts",
+                  "wto_merge"):
             getattr(lib, f).restype = i32
         _lib = lib
     return _lib
@@ -130,6 +132,26 @@ def dd_bits(S: np.ndarray, sigma: int, k: int) -> np.ndarray:
     L, lb = levels(sigma), level_bytes(len(S))
     out = np.zeros((L, lb), dtype=np.uint8)
     _check(_load().wto_dd(_ptr(S), len(S), w, sigma, k, _ptr(out)))
+    return out
+
+
+def merge_bits(parts_bits: list[np.ndarray], parts_n: list[int], parts_hex: list[np.ndarray],
+               sigma: int) -> np.ndarray:
+    """The level bitmaps of the concatenation of k parts, from each part's
+    level bitmaps and node starts (Section 5's buffered build, merged by
+    Algorithm 2's global offsets and Function mergeBA)."""
+    k = len(parts_bits)
+    L = levels(sigma)
+    bits = [np.ascontiguousarray(b, dtype=np.uint8).reshape(-1) for b in parts_bits]
+    hexes = [np.ascontiguousarray(h, dtype=np.uint64) for h in parts_hex]
+    for b, n_, h in zip(bits, parts_n, hexes):
+        if b.size != L * level_bytes(n_) or h.size != (1 << L) + 1:
+            raise OracleError("bad argument")
+    out = np.zeros((L, level_bytes(int(sum(parts_n)))), dtype=np.uint8)
+    bp = (C.c_void_p * k)(*[b.ctypes.data for b in bits])
+    hp = (C.c_void_p * k)(*[h.ctypes.data for h in hexes])
+    ns = (C.c_uint64 * k)(*parts_n)
+    _check(_load().wto_merge(bp, ns, hp, k, sigma, _ptr(out)))
     return out
 
 

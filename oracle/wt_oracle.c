@@ -44,6 +44,11 @@
  *      exclusive upper bound, "dest" and "dst" are one variable, m / k is the
  *      node and m mod k the segment; in createPartialBA "n" is the segment
  *      length.
+ *   R9 in the buffered extension of Section 5 the per-buffer array L of node
+ *      starts is taken as the part's leaf-level node starts Hex (2^L + 1
+ *      entries), from which node v of level i starts at Hex[v << (L - i)];
+ *      the parts may have any lengths, and the result is the tree of their
+ *      concatenation in part order.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -316,6 +321,47 @@ int wto_dd(const void *S, uint64_t n, int w, uint64_t sigma, uint32_t k, uint8_t
         free(pB);
     }
     free(x);
+    return WTO_OK;
+}
+
+/*
+ * The merge of partial trees, run sequentially: the extension of Section 5
+ * (read S in buffers, build a partial tree per buffer, keep each one's node
+ * starts, then merge), whose last two steps are those of Algorithm 2.
+ * Inputs: k parts, part a with part_n[a] symbols, its level bitmaps
+ * part_bits[a] (L padded levels, the layout of wto_build_bits) and its node
+ * starts part_hex[a] (the local offsets: 2^L + 1 entries, as wto_node_starts;
+ * node v of level i starts at part_hex[a][v << (L - i)]).  For each level i:
+ * the prefix sum over the nodes' sizes, node-major and part-minor (the
+ * order of Algorithm 2's global offsets), gives each (part, node) run its
+ * offset in the result; Function mergeBA then copies the run's bits there
+ * (reading R8).  The result is the tree of the concatenation S_0 S_1 ...
+ * S_{k-1}: n = the sum of part_n bits per level.
+ */
+int wto_merge(const uint8_t *const *part_bits, const uint64_t *part_n, const uint64_t *const *part_hex,
+              uint32_t k, uint64_t sigma, uint8_t *bits)
+{
+    if (k == 0 || sigma < 1) return WTO_ERR_ARG;
+    uint32_t L = wto_levels(sigma);
+    uint64_t n = 0;
+    for (uint32_t a = 0; a < k; a++) {
+        if (part_hex[a][0] != 0 || part_hex[a][1ull << L] != part_n[a]) return WTO_ERR_ARG;
+        n += part_n[a];
+    }
+    uint64_t lb = wto_level_bytes(n);
+    memset(bits, 0, L * lb);
+    for (uint32_t i = 0; i < L; i++) {
+        uint64_t nodes = 1ull << i, sh = L - i;
+        uint8_t *B = bits + i * lb;
+        uint64_t go = 0;  /* the running global offset */
+        for (uint64_t v = 0; v < nodes; v++)
+            for (uint32_t a = 0; a < k; a++) {
+                const uint8_t *src = part_bits[a] + i * wto_level_bytes(part_n[a]);
+                uint64_t lo = part_hex[a][v << sh], nb = part_hex[a][(v + 1) << sh] - lo;
+                for (uint64_t t = 0; t < nb; t++) bit_put(B, go + t, bit_get(src, lo + t));
+                go += nb;
+            }
+    }
     return WTO_OK;
 }
 

@@ -295,3 +295,75 @@ def test_node_starts_are_histogram_prefix(sigma):
             hits = np.flatnonzero(keys == v)
             if len(hits):
                 assert hits[0] == hx[v << (L - l)]
+
+
+# ---------------------------------------------------------------- merge of partial trees
+
+def sorted_bits(S, sigma):
+    """Level bitmaps of S from numpy's stable sort (a library routine), padded."""
+    L = O.levels(sigma)
+    n = len(S)
+    out = np.zeros((L, ((n + 511) // 512) * 64), dtype=np.uint8)
+    for l in range(L):
+        P = stable_level_order(S, sigma, l).astype(np.uint64)
+        b = ((P >> np.uint64(L - 1 - l)) & np.uint64(1)).astype(np.uint8)
+        b = np.concatenate([b, np.zeros(out.shape[1] * 8 - n, np.uint8)])
+        out[l] = np.packbits(b, bitorder="little")
+    return out
+
+
+def hist_starts(S, sigma):
+    """Node starts of S from numpy's bincount and cumsum."""
+    H = np.bincount(S, minlength=1 << O.levels(sigma))
+    return np.concatenate([[0], np.cumsum(H)]).astype(np.uint64)
+
+
+@pytest.mark.parametrize("sigma", [1, 2, 5, 20, 96, 256, 300, 65536])
+@pytest.mark.parametrize("cuts", [[0], [777], [0, 0], [300, 0, 700], [1, 1, 1, 1, 1], [513, 2000, 0, 37, 4096]])
+def test_merge_of_partial_trees_is_the_tree_of_the_concatenation(sigma, cuts):
+    """Merging the parts' trees (Section 5, Algorithm 2's offsets, mergeBA)
+    gives the tree of S_0 S_1 ... S_{k-1}: compared with numpy's stable sort of
+    the concatenation.  Parts and node starts come from numpy too, so a
+    part-major copy order, a dropped part or a shifted offset fails here."""
+    rng = np.random.default_rng(sigma + len(cuts))
+    dt = inputs.sym_dtype(sigma)
+    parts = [rng.integers(0, sigma, c).astype(dt) for c in cuts]
+    merged = O.merge_bits([sorted_bits(p, sigma) for p in parts], cuts, [hist_starts(p, sigma) for p in parts],
+                          sigma)
+    S = np.concatenate(parts)
+    assert np.array_equal(merged, sorted_bits(S, sigma))
+
+
+def test_merge_of_skewed_parts_with_empty_nodes():
+    """Parts drawn from disjoint halves of the alphabet: every node of the
+    result is empty in some part, so the node-major order is visible."""
+    sigma = 64
+    a = np.arange(0, 32, dtype=np.uint8).repeat(5)
+    b = np.arange(32, 64, dtype=np.uint8)[::-1].repeat(3)
+    c = np.array([63, 0, 31, 32] * 50, dtype=np.uint8)
+    parts = [a, b, c]
+    merged = O.merge_bits([sorted_bits(p, sigma) for p in parts], [len(p) for p in parts],
+                          [hist_starts(p, sigma) for p in parts], sigma)
+    assert np.array_equal(merged, sorted_bits(np.concatenate(parts), sigma))
+
+
+def test_merge_of_worked_example_in_three_parts():
+    """The worked example of Section 2.2 cut into three parts (as in the dd
+    example of Section 3.2) and merged answers the paper's access(S, 24)."""
+    g, alphabet, S = example()
+    sigma = len(alphabet)
+    parts = [S[:10], S[10:21], S[21:]]
+    merged = O.merge_bits([sorted_bits(p, sigma) for p in parts], [len(p) for p in parts],
+                          [hist_starts(p, sigma) for p in parts], sigma)
+    i = int(g["access_index"])
+    assert int(O.access(merged, len(S), sigma, [i])[0]) == int(g["access_code"])
+    assert alphabet[int(O.access(merged, len(S), sigma, [i])[0])] == g["access_symbol"]
+    assert list(O.access(merged, len(S), sigma, np.arange(len(S)))) == list(S)
+
+
+def test_merge_rejects_inconsistent_node_starts():
+    S = np.array([0, 1, 2, 3], dtype=np.uint8)
+    hx = hist_starts(S, 4)
+    hx[-1] = 5  # does not end at the part's length
+    with pytest.raises(O.OracleError):
+        O.merge_bits([sorted_bits(S, 4)], [4], [hx], 4)
