@@ -26,6 +26,10 @@ cont and rand): n = 2^30 four-byte codes over sigma = 2^y, y in {4, 6, ...,
 14}, each code n / sigma times, in code order (cont) or at random positions
 (rand); one line with the whole set's throughput and each input's rate.
 
+``--workload merge`` runs the buffered build of Section 5 on the default
+sequences: each built in 2^28-symbol chunks whose partial trees are then
+merged (wt_build_chunked), with the merge step's own bandwidth.
+
 ``--impl reference`` times the CPU oracle instead (single thread, bounded
 sample of the same workload).  Under torchrun every rank builds its own
 replica (weak scaling, no collective on the data path); rank 0 prints.
@@ -468,6 +472,110 @@ def run_locality(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+MERGE_CHUNK_LOG2 = 28
+
+
+def run_merge(args, ws, rank, local):
+    """The buffered build of Section 5 on the default sequences: each of the
+    text and DNA sequences (2^30 symbols) built in 2^28-symbol chunks, each
+    chunk into a partial tree, then the partial trees merged into one
+    (wt_build_chunked).  Reports the build rate, the merge step's own
+    bandwidth, and the same build from pinned host buffers end to end."""
+    import torch
+
+    from paper_1610_05994_gb300 import build as B
+    from paper_1610_05994_gb300 import wt as W
+
+    torch.cuda.set_device(local)
+    B.build_library()
+    W.load()
+    dev = torch.device("cuda", local)
+    wls = WORKLOAD_SETS["text+dna"]
+    host = [w.generate(min(w.n, 1 << args.size_log2) if args.size_log2 else None) for w in wls]
+    sigmas = [w.sigma for w in wls]
+    chunk = 1 << (min(MERGE_CHUNK_LOG2, args.size_log2 - 2) if args.size_log2 else MERGE_CHUNK_LOG2)
+    seq_d = [torch.from_numpy(h).to(dev) for h in host]
+    torch.cuda.synchronize()
+
+    def step(src, keep):
+        trees = [W.build_chunked(S, sigma, chunk, wait=False) for S, sigma in zip(src, sigmas)]
+        for t in keep:
+            t.free()
+        return trees
+
+    keep = []
+    for _ in range(args.warmup):
+        keep = step(seq_d, keep)
+    for t in keep:
+        t.wait()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    W.profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        keep = step(seq_d, keep)
+    e1.record()
+    torch.cuda.synchronize()
+    stats = W.profile_end()
+    clk = clocks.stop()
+    for t in keep:
+        t.wait()
+        t.free()
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, ws)
+    syms = sum(h.size for h in host)
+
+    host_p = [torch.from_numpy(h).pin_memory() for h in host]
+    host_np = [p.numpy() for p in host_p]
+    keep = step(host_np, [])
+    for t in keep:
+        t.wait()
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    k2 = max(1, min(args.steps, 3))
+    f0.record()
+    for _ in range(k2):
+        keep = step(host_np, keep)
+    f1.record()
+    torch.cuda.synchronize()
+    for t in keep:
+        t.wait()
+        t.free()
+    ms_e2e = reduce_max(f0.elapsed_time(f1) / k2, ws)
+    if rank != 0:
+        return
+    roofline, kernels, launches = roofline_of(stats, args.steps)
+    mg = stats.get("merge")
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs") or 6800.0
+    merge = None
+    if mg and mg["total_ms"] > 0:
+        gbs = mg["alg_bytes"] / (mg["total_ms"] * 1e-3) / 1e9
+        merge = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                 "alg_bytes_per_launch": mg["alg_bytes"] / mg["launches"],
+                 "avg_launch_ms": mg["total_ms"] / mg["launches"],
+                 "bytes_model": "per merged level of n bits: read the parts' bits n/8, write the level n/8 "
+                                "and its directory n/128"}
+    line = {"metric": METRIC, "value": job_rate(syms, ws, ms), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"buffered build (Section 5): u8 text n={host[0].size} sigma=96 Zipf(1.0) + "
+                                   f"u8 DNA n={host[1].size} sigma=4 uniform, each in chunks of {chunk} symbols "
+                                   f"built alone, then merged",
+                       "chunk": chunk, "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2; no flush"},
+            "roofline": roofline, "merge_roofline": merge, "cpu_baseline": None,
+            "e2e": {"value": job_rate(syms, ws, ms_e2e), "unit": UNIT,
+                    "h2d_bytes_per_step": sum(h.nbytes for h in host), "d2h_bytes_per_step": 0,
+                    "ms_per_step": ms_e2e},
+            "gpu_launches": launches, "clocks": clk, "kernels": kernels}
+    print(json.dumps(line), flush=True)
+
+
 def roofline_of(stats: dict, steps: int):
     """Roofline of the kernel with the largest device time, per-kernel
     figures per step, and the number of library launches, from the library's
@@ -795,7 +903,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + ["batch", "serve", "locality"],
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + ["batch", "serve", "locality", "merge"],
                     default="text+dna")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured build requests")
     ap.add_argument("--size-log2", type=int, default=0,
@@ -805,7 +913,7 @@ def main():
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
-        if args.workload in ("batch", "serve", "locality"):
+        if args.workload in ("batch", "serve", "locality", "merge"):
             print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed on the single-sequence "
                               "workloads only"}), flush=True)
             return
@@ -815,7 +923,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        {"batch": run_batch, "serve": run_serve, "locality": run_locality}.get(args.workload, run_ours)(
+        {"batch": run_batch, "serve": run_serve, "locality": run_locality, "merge": run_merge}.get(
+            args.workload, run_ours)(
             args, ws, rank, local)
     finally:
         if ws > 1:

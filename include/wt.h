@@ -119,6 +119,43 @@ wt_status wt_build_batch(const void *const *S, const uint64_t *n, const uint64_t
                          const int *sym_width, uint32_t count, wt_handle *out, void *stream);
 
 /*
+ * Merge of partial trees (the buffered build of Section 5, finished with
+ * Algorithm 2's global offsets and Function mergeBA, Section 3.2): returns
+ * the tree of the concatenation S_0 S_1 ... S_{k-1} of the parts' sequences,
+ * in the order of parts[0..k).  parts is a host array of k handles (1 <= k
+ * <= 65536) with the same sigma and sym_width and a total length below
+ * 2^56; anything else gives WT_ERR_ARG.  The call first waits on the host
+ * for every part's build and fails with the first part's error status, if
+ * any; then it enqueues the merge on stream and returns (wt_wait completes
+ * it).  The parts stay owned by the caller and must stay resident until the
+ * merge has completed: free them after wt_wait on the result, or free them
+ * in order on the merge's stream.  The trees keep no node offsets
+ * (Section 2.2), so each part's node starts are recovered from its bitmaps
+ * by rank; parts whose bitmaps and directories are inconsistent give
+ * WT_ERR_ARG from wt_wait.  Device scratch: k (2^L + 1) node starts of 8
+ * bytes plus the directory scan's per-unit counts.  The result's layout is
+ * the one above, bit for bit the tree a single build of the concatenation
+ * gives.
+ */
+wt_handle wt_merge_async(const wt_handle *parts, uint32_t k, void *stream);
+
+/*
+ * Buffered build (Section 5): builds S[0..n) in chunks of at most `chunk`
+ * symbols, each chunk's tree built alone (as wt_build_async), then merges
+ * them (as wt_merge_async); the partial trees are freed in stream order
+ * after the merge.  At most two chunks' builds are in flight, so a host S is
+ * staged on the device at most two chunks at a time and the level-wise
+ * scratch is that of one chunk; the partial trees together take about the
+ * size of the final tree.  Arguments as wt_build_async, plus chunk >= 1 and
+ * ceil(n / chunk) <= 65536 (else WT_ERR_ARG).  Waits on the host for the
+ * chunks' builds and returns with the merge enqueued on stream (wt_wait
+ * completes it); a failed chunk (for example WT_ERR_SYMBOL_RANGE) fails the
+ * call.  S must stay valid until the call returns.
+ */
+wt_handle wt_build_chunked(const void *S, uint64_t n, uint64_t sigma, int sym_width, uint64_t chunk,
+                           void *stream);
+
+/*
  * access(i) for m device positions i[k] -> out[k] (device, uint32) by the
  * top-down walk of Section 2.2 simulated with rank on the level bitmaps.
  * i[k] >= n gives UINT32_MAX.

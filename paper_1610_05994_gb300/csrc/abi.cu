@@ -79,11 +79,11 @@ double level_step_bytes(uint64_t n, int w, bool has_next) {
 // kernel.
 enum KernelId {
     K_HIST = 0, K_NODE_STARTS, K_NODE_TABLES, K_LEVEL_PASS, K_DD_COUNT, K_DD_SCAN, K_DD_WRITE,
-    K_Q_ACCESS, K_Q_RANK, K_Q_SELECT, K_Q_MULTI, K_COUNT
+    K_Q_ACCESS, K_Q_RANK, K_Q_SELECT, K_Q_MULTI, K_MERGE_STARTS, K_MERGE, K_COUNT
 };
-const char *kKernelNames[K_COUNT] = {"histogram", "node_starts", "node_tables", "level_pass", "dd_count",
-                                     "dd_scan",   "dd_write",    "query_access", "query_rank", "query_select",
-                                     "query_multi"};
+const char *kKernelNames[K_COUNT] = {"histogram",  "node_starts", "node_tables",  "level_pass",   "dd_count",
+                                     "dd_scan",    "dd_write",    "query_access", "query_rank",   "query_select",
+                                     "query_multi", "merge_starts", "merge"};
 
 struct ProfRecord {
     int kid;
@@ -485,6 +485,8 @@ wt_status finalize(wt_tree *t) {
         t->status = WT_ERR_SYMBOL_RANGE;
     else if (err & kErrTimeout)
         t->status = WT_ERR_TIMEOUT;
+    else if (err & kErrBound)
+        t->status = WT_ERR_ARG;
     return t->status;
 }
 
@@ -979,6 +981,189 @@ wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int 
     return t;
 }
 
+// ------------------------------------------------------------- merges
+
+// Algorithmic bytes of one merged level of n bits: read the parts' bits,
+// write the level and its directory.
+double merge_level_bytes(uint64_t n) { return n / 8.0 + n / 8.0 + n / 128.0; }
+
+// Creates the handle of a tree of n symbols (memory allocated, descriptor
+// filled, nothing enqueued).
+wt_status tree_create(uint64_t n, uint64_t sigma, int width, cudaStream_t st, wt_tree **out) {
+    wt_tree *t = new (std::nothrow) wt_tree();
+    if (!t) return WT_ERR_OOM;
+    t->n = n;
+    t->sigma = sigma;
+    t->L = levels_of(sigma);
+    t->width = width;
+    t->stream = st;
+    t->alloc = current_allocator();
+    if (cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete t;
+        return WT_ERR_CUDA;
+    }
+    const wt_status r = tree_alloc(t, st);
+    if (r != WT_OK) {
+        t->finalized = true;
+        tree_destroy(t);
+        return r;
+    }
+    *out = t;
+    return WT_OK;
+}
+
+// Enqueues the merge of k finished parts into t (allocated, n = the parts'
+// total): every part's node starts, then per level the bits (merge.cu) and
+// the directory (the level step's count from the bitmap and its scans).
+wt_status enqueue_merge(wt_tree *t, const wt_handle *parts, uint32_t k, cudaStream_t st) {
+    WT_CK(cudaMemcpyAsync(t->d_desc, &t->h_desc, sizeof(TreeDesc), cudaMemcpyHostToDevice, st));
+    WT_CK(cudaMemsetAsync(t->d_err, 0, sizeof(uint32_t), st));
+    if (t->n == 0 || t->L == 0) {
+        for (uint32_t l = 0; l < t->L; l++) {
+            WT_CK(cudaMemsetAsync(t->h_desc.lv[l].R, 0, 4, st));
+            WT_CK(cudaMemsetAsync(t->h_desc.lv[l].Hy, 0, 8, st));
+        }
+        return WT_OK;
+    }
+    const uint64_t stride = (1ull << t->L) + 1;
+    const size_t ptrs = align256(k * sizeof(TreeDesc *));
+    const size_t hex = align256((size_t)k * stride * 8);
+    const size_t hexm = align256(stride * 8);
+    const size_t counts = align256(lw_counts_bytes(t->n, t->width));
+    const size_t prefix = align256(lw_prefix_bytes(t->n, t->width));
+    const size_t jslot = level_job_slot_bytes();
+    const size_t bytes = ptrs + hex + hexm + counts + prefix + jslot;
+    char *mem = static_cast<char *>(dev_alloc(t->alloc, bytes, st));
+    if (!mem) return WT_ERR_OOM;
+    const TreeDesc **d_parts = reinterpret_cast<const TreeDesc **>(mem);
+    uint64_t *d_hex = reinterpret_cast<uint64_t *>(mem + ptrs);
+    uint64_t *d_hexm = reinterpret_cast<uint64_t *>(mem + ptrs + hex);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(mem + ptrs + hex + hexm);
+    uint64_t *pre = reinterpret_cast<uint64_t *>(mem + ptrs + hex + hexm + counts);
+    void *job_slot = mem + ptrs + hex + hexm + counts + prefix;
+    std::vector<const TreeDesc *> hp(k);
+    for (uint32_t a = 0; a < k; a++) hp[a] = parts[a]->d_desc;
+    wt_status r = WT_OK;
+    if (cudaMemcpyAsync(d_parts, hp.data(), k * sizeof(TreeDesc *), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    if (r == WT_OK) {
+        ProfScope p(K_MERGE_STARTS, 8.0 * (k + 1) * stride, st);
+        if (launch_merge_starts(d_parts, k, t->L, d_hex, d_hexm, t->d_err, st) != cudaSuccess) r = WT_ERR_CUDA;
+    }
+    for (uint32_t l = 0; l < t->L && r == WT_OK; l++) {
+        ProfScope p(K_MERGE, merge_level_bytes(t->n), st);
+        // With L = l + 1 the level step counts from the bitmap and scans
+        // (R, Hy, S1, S0, ones) without a pass; the node tables are unused.
+        if (launch_merge_level(d_parts, k, t->L, l, d_hex, d_hexm, t->n, t->h_desc.lv[l].words, t->d_err, st) !=
+                cudaSuccess ||
+            launch_level_pass(nullptr, nullptr, t->n, t->width, l + 1, l, d_hexm, d_hexm, t->h_desc.lv[l],
+                              &t->d_desc->lv[l].ones, cnt, pre, true, nullptr, t->d_err, job_slot, st) !=
+                cudaSuccess)
+            r = WT_ERR_CUDA;
+    }
+    if (r != WT_OK) cudaGetLastError();
+    dev_free(t->alloc, mem, bytes, st);
+    return r;
+}
+
+// Largest number of parts of one merge (its scratch holds k (2^L + 1) node
+// starts).
+constexpr uint32_t kMaxMergeParts = 1u << 16;
+
+wt_handle merge_async(const wt_handle *parts, uint32_t k, cudaStream_t st) {
+    if (!parts || k == 0 || k > kMaxMergeParts || !parts[0]) {
+        set_last(WT_ERR_ARG);
+        return nullptr;
+    }
+    uint64_t n = 0;
+    for (uint32_t a = 0; a < k; a++) {
+        if (!parts[a] || parts[a]->sigma != parts[0]->sigma || parts[a]->width != parts[0]->width) {
+            set_last(WT_ERR_ARG);
+            return nullptr;
+        }
+        n += parts[a]->n;
+    }
+    if (n >= (1ull << 56)) {
+        set_last(WT_ERR_ARG);
+        return nullptr;
+    }
+    // The parts' builds must have completed (and succeeded) first.
+    for (uint32_t a = 0; a < k; a++) {
+        const wt_status ps = finalize(parts[a]);
+        if (ps != WT_OK) {
+            set_last(ps);
+            return nullptr;
+        }
+    }
+    wt_tree *t = nullptr;
+    wt_status r = tree_create(n, parts[0]->sigma, parts[0]->width, st, &t);
+    if (r != WT_OK) {
+        set_last(r);
+        return nullptr;
+    }
+    t->variant = parts[0]->variant;
+    r = enqueue_merge(t, parts, k, st);
+    if (r == WT_OK && cudaEventRecord(t->done, st) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    if (r != WT_OK) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        t->finalized = true;
+        tree_destroy(t);
+        set_last(r);
+        return nullptr;
+    }
+    set_last(WT_OK);
+    return t;
+}
+
+// The buffered build of Section 5: S in chunks of at most `chunk` symbols,
+// each built alone into a partial tree, then one merge.  At most two
+// chunks' builds are in flight, so at most two chunks of host symbols are
+// staged on the device at a time.
+wt_handle build_chunked(const void *S, uint64_t n, uint64_t sigma, int width, uint64_t chunk, cudaStream_t st) {
+    wt_status r = check_args(S, n, sigma, width);
+    if (r == WT_OK && chunk == 0) r = WT_ERR_ARG;
+    const uint64_t k = (r == WT_OK && n) ? ceil_div(n, chunk) : 1;
+    if (r == WT_OK && k > kMaxMergeParts) r = WT_ERR_ARG;
+    if (r != WT_OK) {
+        set_last(r);
+        return nullptr;
+    }
+    if (k == 1) return build_async(S, n, sigma, width, WT_VARIANT_AUTO, st);
+    std::vector<wt_handle> parts;
+    parts.reserve(k);
+    const char *base = static_cast<const char *>(S);
+    for (uint64_t a = 0; a < k && r == WT_OK; a++) {
+        const uint64_t lo = a * chunk, len = (lo + chunk < n ? chunk : n - lo);
+        wt_handle h = build_async(base + lo * (uint64_t)width, len, sigma, width, WT_VARIANT_AUTO, st);
+        if (!h) {
+            r = g_last;
+            break;
+        }
+        parts.push_back(h);
+        if (a >= 2) r = finalize(parts[a - 2]);
+    }
+    wt_handle out = nullptr;
+    if (r == WT_OK) {
+        out = merge_async(parts.data(), (uint32_t)k, st);
+        if (!out) r = g_last;
+    }
+    if (r != WT_OK) cudaStreamSynchronize(st);
+    // The parts' memory returns in stream order after the merge has read it.
+    for (wt_handle h : parts) {
+        h->finalized = true;
+        tree_destroy(h);
+    }
+    set_last(r);
+    return out;
+}
+
 }  // namespace
 
 namespace wt {
@@ -1018,6 +1203,14 @@ wt_status wt_build_batch(const void *const *S, const uint64_t *n, const uint64_t
                          uint32_t count, wt_handle *out, void *stream) {
     if (count > 0 && (!S || !n || !sigma || !sym_width || !out)) return set_last(WT_ERR_ARG);
     return set_last(build_batch_impl(S, n, sigma, sym_width, count, out, static_cast<cudaStream_t>(stream)));
+}
+
+wt_handle wt_merge_async(const wt_handle *parts, uint32_t k, void *stream) {
+    return merge_async(parts, k, static_cast<cudaStream_t>(stream));
+}
+
+wt_handle wt_build_chunked(const void *S, uint64_t n, uint64_t sigma, int sym_width, uint64_t chunk, void *stream) {
+    return build_chunked(S, n, sigma, sym_width, chunk, static_cast<cudaStream_t>(stream));
 }
 
 wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, void *stream) {

@@ -17,38 +17,6 @@ namespace wt {
 
 constexpr int kQueryThreads = 256;
 
-// ones in B[0, 512 b): hyper entry plus the wrapped 32-bit block entry.
-__device__ __forceinline__ uint64_t ones_before_block(const LevelDesc &d, uint64_t b) {
-    const uint64_t hy = d.Hy[(b << 9) >> kSpanShift];
-    return hy + (uint32_t)(d.R[b] - (uint32_t)hy);
-}
-
-// ones in B[0, i), 0 <= i <= n.
-__device__ __forceinline__ uint64_t rank1(const LevelDesc &d, uint64_t i) {
-    const uint64_t b = i >> 9;
-    uint64_t r = ones_before_block(d, b);
-    const uint32_t rem = (uint32_t)(i & 511);
-    if (rem) {
-        const uint4 *blk = reinterpret_cast<const uint4 *>(d.words + b * 16);
-        const uint32_t full = rem >> 5, part = rem & 31;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            if ((uint32_t)q * 4 > full) break;
-            const uint4 x = __ldg(blk + q);
-            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t idx = q * 4 + k;
-                if (idx < full)
-                    r += __popc(w[k]);
-                else if (idx == full && part)
-                    r += __popc(w[k] & ((1u << part) - 1u));
-            }
-        }
-    }
-    return r;
-}
-
 __device__ __forceinline__ uint32_t bit_at(const LevelDesc &d, uint64_t p) {
     return (__ldg(d.words + (p >> 5)) >> (p & 31)) & 1u;
 }

@@ -24,6 +24,7 @@ constexpr uint32_t kBlocksPerSpanMask = (1u << (kSpanShift - 9)) - 1;
 // Device error word bits (OR-ed by kernels, read by the host after a build).
 constexpr uint32_t kErrSymbol = 1u;
 constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrBound = 4u;  // a merge found parts whose node starts do not fit their bitmaps
 
 struct LevelDesc {
     uint32_t *words;  // ceil(n/512) * 16
@@ -50,6 +51,41 @@ __host__ __device__ inline uint32_t levels_of(uint64_t sigma) {
     uint32_t L = 0;
     while (L < 63 && (1ull << L) < sigma) L++;
     return L;
+}
+
+// ------------------------------------------------------- rank on a level
+// (query.cu, merge.cu)
+
+// ones in B[0, 512 b): hyper entry plus the wrapped 32-bit block entry.
+__device__ __forceinline__ uint64_t ones_before_block(const LevelDesc &d, uint64_t b) {
+    const uint64_t hy = d.Hy[(b << 9) >> kSpanShift];
+    return hy + (uint32_t)(d.R[b] - (uint32_t)hy);
+}
+
+// ones in B[0, i), 0 <= i <= n.
+__device__ __forceinline__ uint64_t rank1(const LevelDesc &d, uint64_t i) {
+    const uint64_t b = i >> 9;
+    uint64_t r = ones_before_block(d, b);
+    const uint32_t rem = (uint32_t)(i & 511);
+    if (rem) {
+        const uint4 *blk = reinterpret_cast<const uint4 *>(d.words + b * 16);
+        const uint32_t full = rem >> 5, part = rem & 31;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if ((uint32_t)q * 4 > full) break;
+            const uint4 x = __ldg(blk + q);
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t idx = q * 4 + k;
+                if (idx < full)
+                    r += __popc(w[k]);
+                else if (idx == full && part)
+                    r += __popc(w[k] & ((1u << part) - 1u));
+            }
+        }
+    }
+    return r;
 }
 
 // ------------------------------------------------------- TMA + mbarrier
@@ -312,6 +348,17 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
                               uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
                               cudaStream_t st, bool counted = false);
+
+// Merge of partial trees (merge.cu).  parts: device array of k device
+// descriptors of trees with the same alphabet.  launch_merge_starts
+// recovers every part's node starts into hex (k x (2^L + 1) uint64) and
+// their sums into hex_out (2^L + 1); launch_merge_level writes level l of the
+// concatenation (n bits, padded to whole 512-bit blocks) into words.
+cudaError_t launch_merge_starts(const TreeDesc *const *parts, uint32_t k, uint32_t L, uint64_t *hex,
+                                uint64_t *hex_out, uint32_t *err, cudaStream_t st);
+cudaError_t launch_merge_level(const TreeDesc *const *parts, uint32_t k, uint32_t L, uint32_t l, const uint64_t *hex,
+                               const uint64_t *hex_out, uint64_t n, uint32_t *words, uint32_t *err,
+                               cudaStream_t st);
 
 // Kernel (d): dd-direct build of all levels for small sigma (dd.cu).
 struct DdScratch {

@@ -59,6 +59,8 @@ _SIGNATURES = [
     ("wt_wait", C.c_int, [C.c_void_p]),
     ("wt_build_batch", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
                                  C.c_void_p]),
+    ("wt_merge_async", C.c_void_p, [C.c_void_p, C.c_uint32, C.c_void_p]),
+    ("wt_build_chunked", C.c_void_p, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_void_p]),
     ("wt_access", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
     ("wt_rank", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
     ("wt_select", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
@@ -281,6 +283,42 @@ def build_batch(seqs: list[torch.Tensor], sigmas: list[int], stream=None, wait: 
         for t in trees:
             t.wait()
     return trees
+
+
+def merge(parts: list[Tree], stream=None, wait: bool = True) -> Tree:
+    """The tree of the concatenation of the parts' sequences (wt_merge_async).
+    The parts stay valid; free them only after the merge has completed."""
+    lib = load()
+    if not parts:
+        raise WTError(ERR_ARG, "wt_merge_async")
+    hs = (C.c_void_p * len(parts))(*[t.handle for t in parts])
+    h = lib.wt_merge_async(hs, len(parts), C.c_void_p(_stream(stream)))
+    if not h:
+        raise WTError(lib.wt_last_status(), "wt_merge_async")
+    t = Tree(h, sum(p.n for p in parts), parts[0].sigma, parts[0].width)
+    if wait:
+        t.wait()
+    return t
+
+
+def build_chunked(S, sigma: int, chunk: int, stream=None, wait: bool = True) -> Tree:
+    """Builds from a CUDA tensor or numpy array in chunks of at most `chunk`
+    symbols, merged into one tree (wt_build_chunked)."""
+    lib = load()
+    if isinstance(S, np.ndarray):
+        S = np.ascontiguousarray(S)
+        width, ptr, n = S.dtype.itemsize, S.ctypes.data, S.size
+    else:
+        if S.dtype not in (torch.uint8, torch.uint16, torch.uint32, torch.int32, torch.int16):
+            raise TypeError("symbols must be 8, 16 or 32-bit unsigned codes")
+        width, ptr, n = S.element_size(), _dptr(S), S.numel()
+    h = lib.wt_build_chunked(C.c_void_p(ptr), n, sigma, width, chunk, C.c_void_p(_stream(stream)))
+    if not h:
+        raise WTError(lib.wt_last_status(), "wt_build_chunked")
+    t = Tree(h, n, sigma, width)
+    if wait:
+        t.wait()
+    return t
 
 
 def query_multi(trees: list[Tree], tree_idx: torch.Tensor, op: torch.Tensor, c: torch.Tensor, arg: torch.Tensor,
