@@ -77,7 +77,9 @@ __global__ void merge_starts_kernel(const TreeDesc *const *__restrict__ parts, u
         uint64_t *h = hex + a * stride;
         const uint64_t b = h[v << s], e = h[(v + 1) << s];
         uint64_t z = 0;
-        if (e > b) {
+        if (e < b) {
+            bad = true;
+        } else if (e > b) {
             const TreeDesc *d = parts[a];
             if (e > d->n) {
                 bad = true;
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_level_kernel(MergeLevel m
                 if (d + len - pos < cnt) cnt = d + len - pos;
                 if (end - pos < cnt) cnt = end - pos;
                 const uint64_t sp = src + (pos - d);  // the piece's first source bit
-                if (sp + cnt > pn) {
+                if (sp >= pn || pn - sp < cnt) {
                     bad = true;
                     pos = end;
                     break;
