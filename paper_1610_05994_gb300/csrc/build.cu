@@ -47,8 +47,11 @@ __device__ __forceinline__ void level0_vector(const Level0Fuse &z, uint64_t k, c
     if ((threadIdx.x & 31) == 0) z.cnt[k / 32] = c;
 }
 
+// Whole tiles only: the level step's scan reads every unit count of every
+// tile, and the histogram writes the counts of the units it covers.
 bool level0_fusable(const void *S, uint64_t n, int width, uint64_t sigma) {
-    return width == 1 && sigma >= 2 && n > 0 && n % 512 == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0;
+    return width == 1 && sigma >= 2 && n > 0 && n % lw_tile_elems(1) == 0 &&
+           (reinterpret_cast<uintptr_t>(S) & 15) == 0;
 }
 
 // Shared-memory histogram: `copies` private copies of the sigma bins (warp w

@@ -15,9 +15,11 @@
 // part-minor.  A thread writes 128 consecutive bits of the result with one
 // 16-byte store.  It finds the node that holds its first bit by binary
 // search over the result's node starts and the part by walking that node's
-// runs, then copies pieces of at most 32 bits (one or two source words each,
-// never crossing an output word) until its 128 bits are done, moving to the
-// next part's run and, when a node is exhausted, searching again.  Where
+// runs.  A group inside one run is a funnel shift of five source words;
+// otherwise the thread copies pieces of at most 32 bits (one or two source
+// words each, never crossing an output word) until its 128 bits are done,
+// moving to the next part's run and, when a node is exhausted, searching
+// again.  Where
 // mergeBA writes each run's boundary words atomically, here every output
 // word has exactly one writer: no atomics, and the padding bits beyond n are
 // written as zeros by the same stores.
@@ -167,6 +169,24 @@ __global__ void __launch_bounds__(kMergeThreads) merge_level_kernel(MergeLevel m
             const TreeDesc *P = m.parts[a];
             const uint32_t *sw = P->lv[m.l].words;
             uint64_t pn = P->n;
+            if (end - pos == 128 && d + len - pos >= 128) {
+                // The whole group lies in one run: a funnel shift of five
+                // consecutive source words.
+                const uint64_t sp = src + (pos - d);
+                if (sp >= pn || pn - sp < 128) {
+                    bad = true;
+                    break;
+                }
+                const uint32_t so = (uint32_t)(sp & 31);
+                const uint32_t *q = sw + (sp >> 5);
+                const uint32_t x0 = __ldg(q), x1 = __ldg(q + 1), x2 = __ldg(q + 2), x3 = __ldg(q + 3);
+                const uint32_t x4 = so ? __ldg(q + 4) : 0u;
+                w[0] = __funnelshift_r(x0, x1, so);
+                w[1] = __funnelshift_r(x1, x2, so);
+                w[2] = __funnelshift_r(x2, x3, so);
+                w[3] = __funnelshift_r(x3, x4, so);
+                break;
+            }
             bool node_done = false;
             while (pos < end && !node_done) {
                 const uint32_t off = (uint32_t)(pos & 31);

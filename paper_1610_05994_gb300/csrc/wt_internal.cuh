@@ -262,7 +262,7 @@ struct BuildScratch {
 // Kernel (a): histogram of S into hist (zeroed by the caller) and the symbol
 // range check; then the exclusive scan into hex.
 // Level 0's count pass folded into the histogram's read of S (1-byte
-// symbols, S 16-byte aligned, n a multiple of 512): the level-0 bit (bit
+// symbols, S 16-byte aligned, n a multiple of the 8192-symbol tile): the level-0 bit (bit
 // bsh) of every symbol goes to level 0's bitmap (words), the ones of every
 // 512-symbol unit to cnt (the count pass's layout), and level 1's bitmap is
 // zeroed (next, when level 0's pass writes it; else nullptr).

@@ -67,6 +67,23 @@ def test_wide_symbols(sigma, dtype, n):
     compare_tree(t, S, sigma)
 
 
+@pytest.mark.parametrize("n", [512, 1024, 4608, 8704, 65536 - 512, 65536])
+def test_level0_count_with_a_partial_last_tile_on_reused_memory(n):
+    """n a multiple of 512 (but not always of the 8192-symbol tile): every
+    unit count the level step scans must be written by this build, also when
+    its scratch reuses memory that held another build's counts (the big tree
+    is freed in stream order just before, so its memory comes back)."""
+    W = wt()
+    big = to_dev(inputs.uniform(1 << 22, 256, 9, np.uint8))
+    S = inputs.zipf(n, 96, 1.0, n, np.uint8)
+    D = to_dev(S)
+    for _ in range(3):
+        W.Tree.build(big, 256, wait=False).free()
+        t = W.Tree.build(D, 96, wait=False)
+        t.wait()
+        compare_tree(t, S, 96)
+
+
 def test_host_input_and_unaligned_device_input():
     """S may be host memory; a device S that is not 16-byte aligned takes the scalar path."""
     W = wt()
