@@ -58,9 +58,13 @@ def _load():
         lib.wto_access_trace.argtypes = [vp, u64, u64, u64, vp, vp]
         lib.wto_node_starts.argtypes = [vp, u64, i32, u64, vp]
         lib.wto_merge.argtypes = [vp, vp, vp, u32, u64, vp]
+        lib.wto_wm_build.argtypes = [vp, u64, i32, u64, vp]
+        lib.wto_wm_access.argtypes = [vp, u64, u64, vp, u64, vp]
+        lib.wto_wm_rank.argtypes = [vp, u64, u64, vp, vp, u64, vp]
+        lib.wto_wm_select.argtypes = [vp, u64, u64, vp, vp, u64, vp]
         for f in ("wto_level_order", "wto_build_bits", "wto_pwt", "wto_dd", "wto_directory",
                   "wto_access", "wto_rank", "wto_select", "wto_level_symbol", "wto_access_trace", "wto_node_starts",
-                  "wto_merge"):
+                  "wto_merge", "wto_wm_build", "wto_wm_access", "wto_wm_rank", "wto_wm_select"):
             getattr(lib, f).restype = i32
         _lib = lib
     return _lib
@@ -152,6 +156,41 @@ def merge_bits(parts_bits: list[np.ndarray], parts_n: list[int], parts_hex: list
     hp = (C.c_void_p * k)(*[h.ctypes.data for h in hexes])
     ns = (C.c_uint64 * k)(*parts_n)
     _check(_load().wto_merge(bp, ns, hp, k, sigma, _ptr(out)))
+    return out
+
+
+def wm_bits(S: np.ndarray, sigma: int) -> np.ndarray:
+    """The wavelet matrix's L level bitmaps as a (L, level_bytes(n)) uint8 array."""
+    S, w = _seq(S)
+    L, lb = levels(sigma), level_bytes(len(S))
+    out = np.zeros((L, lb), dtype=np.uint8)
+    _check(_load().wto_wm_build(_ptr(S), len(S), w, sigma, _ptr(out)))
+    return out
+
+
+def wm_access(bits: np.ndarray, n: int, sigma: int, i) -> np.ndarray:
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    i = np.ascontiguousarray(i, dtype=np.uint64)
+    out = np.empty(len(i), dtype=np.uint32)
+    _check(_load().wto_wm_access(_ptr(bits), n, sigma, _ptr(i), len(i), _ptr(out)))
+    return out
+
+
+def wm_rank(bits: np.ndarray, n: int, sigma: int, c, i) -> np.ndarray:
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    c = np.ascontiguousarray(c, dtype=np.uint32)
+    i = np.ascontiguousarray(i, dtype=np.uint64)
+    out = np.empty(len(i), dtype=np.uint64)
+    _check(_load().wto_wm_rank(_ptr(bits), n, sigma, _ptr(c), _ptr(i), len(i), _ptr(out)))
+    return out
+
+
+def wm_select(bits: np.ndarray, n: int, sigma: int, c, j) -> np.ndarray:
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    c = np.ascontiguousarray(c, dtype=np.uint32)
+    j = np.ascontiguousarray(j, dtype=np.uint64)
+    out = np.empty(len(j), dtype=np.uint64)
+    _check(_load().wto_wm_select(_ptr(bits), n, sigma, _ptr(c), _ptr(j), len(j), _ptr(out)))
     return out
 
 

@@ -49,6 +49,10 @@
  *      entries), from which node v of level i starts at Hex[v << (L - i)];
  *      the parts may have any lengths, and the result is the tree of their
  *      concatenation in part order.
+ *   R10 the wavelet matrix (named in Section 5, defined by Claude and
+ *      Navarro 2012) takes level l to hold bit L-1-l, most significant
+ *      first like the tree, with zeros first on the next level, and the
+ *      tree's bitmap layout and directory; sigma = 1 gives no levels.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -614,4 +618,127 @@ int wto_level_symbol(const void *S, uint64_t n, int w, uint64_t sigma, uint32_t 
         }
     }
     return WTO_ERR_ARG;
+}
+
+/* ------------------------------------------------------ wavelet matrix */
+
+/*
+ * The wavelet matrix, the level-wise variant Section 5 names for future work
+ * (Claude and Navarro, SPIRE 2012), written from its definition: S_0 = S;
+ * level l stores bit L-1-l of every symbol of S_l (the same bit as the
+ * tree's level l); S_{l+1} is the whole of S_l stably partitioned by that
+ * bit, zeros first (one node per level, where the tree partitions inside
+ * each node).  Z_l = zeros of level l.  The bitmaps use the tree's padded
+ * layout, so wto_directory applies unchanged (reading R10).
+ */
+int wto_wm_build(const void *S, uint64_t n, int w, uint64_t sigma, uint8_t *bits)
+{
+    uint32_t *x = NULL;
+    int st = load_codes(S, n, w, sigma, &x);
+    if (st) return st;
+    uint32_t L = wto_levels(sigma);
+    uint64_t lb = wto_level_bytes(n);
+    memset(bits, 0, L * lb);
+    uint32_t *nxt = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    if (!nxt) { free(x); return WTO_ERR_NOMEM; }
+    for (uint32_t l = 0; l < L; l++) {
+        uint8_t *B = bits + l * lb;
+        uint64_t k = 0;
+        for (uint64_t p = 0; p < n; p++) bit_put(B, p, level_bit(x[p], L, l));
+        for (uint64_t p = 0; p < n; p++) if (!level_bit(x[p], L, l)) nxt[k++] = x[p];
+        for (uint64_t p = 0; p < n; p++) if (level_bit(x[p], L, l)) nxt[k++] = x[p];
+        uint32_t *tmp = x; x = nxt; nxt = tmp;
+    }
+    free(x);
+    free(nxt);
+    return WTO_OK;
+}
+
+/*
+ * access(i) on the matrix: on level l read the bit b at p; a 0 moves p to
+ * rank0(p) (its place among the zeros, which come first on level l + 1), a 1
+ * to Z_l + rank1(p).  The bits read, most significant first, spell the symbol.
+ */
+int wto_wm_access(const uint8_t *bits, uint64_t n, uint64_t sigma, const uint64_t *I, uint64_t m, uint32_t *out)
+{
+    uint32_t L = wto_levels(sigma);
+    tree_t t;
+    int st = tree_init(&t, bits, n, L);
+    if (st) return st;
+    for (uint64_t q = 0; q < m; q++) {
+        uint64_t p = I[q];
+        if (p >= n) { out[q] = UINT32_MAX; continue; }
+        uint32_t sym = 0;
+        for (uint32_t l = 0; l < L; l++) {
+            int bit = bit_get(bits + l * t.lb, p);
+            p = bit ? rank0(&t, l, n) + rank1(&t, l, p) : rank0(&t, l, p);
+            sym = (sym << 1) | (uint32_t)bit;
+        }
+        out[q] = sym;
+    }
+    tree_free(&t);
+    return WTO_OK;
+}
+
+/*
+ * rank_c(i) on the matrix: the symbols equal to c form one contiguous range
+ * of each level; follow the range [b, e) = [0, i) of the prefix: a 0 bit of
+ * c maps both ends by rank0, a 1 bit by Z_l + rank1.  The answer is e - b at
+ * the bottom.
+ */
+int wto_wm_rank(const uint8_t *bits, uint64_t n, uint64_t sigma, const uint32_t *C, const uint64_t *I,
+                uint64_t m, uint64_t *out)
+{
+    uint32_t L = wto_levels(sigma);
+    tree_t t;
+    int st = tree_init(&t, bits, n, L);
+    if (st) return st;
+    for (uint64_t q = 0; q < m; q++) {
+        uint64_t c = C[q], i = I[q];
+        if (c >= sigma || i > n) { out[q] = UINT64_MAX; continue; }
+        uint64_t b = 0, e = i;
+        for (uint32_t l = 0; l < L; l++) {
+            int bit = (int)((c >> (L - 1 - l)) & 1);
+            if (bit) { b = rank0(&t, l, n) + rank1(&t, l, b); e = rank0(&t, l, n) + rank1(&t, l, e); }
+            else { b = rank0(&t, l, b); e = rank0(&t, l, e); }
+        }
+        out[q] = e - b;
+    }
+    tree_free(&t);
+    return WTO_OK;
+}
+
+/*
+ * select_c(j) on the matrix: walk down from b = 0 by the bits of c (as in
+ * rank) to the start b_L of c's range at the bottom; the answer's position
+ * there is b_L + j - 1 if the range holds j symbols.  Then climb: a position
+ * pos on level l + 1 that came from a 0 bit is the (pos + 1)-th zero of
+ * level l; one from a 1 bit is the (pos - Z_l + 1)-th one.
+ */
+int wto_wm_select(const uint8_t *bits, uint64_t n, uint64_t sigma, const uint32_t *C, const uint64_t *J,
+                  uint64_t m, uint64_t *out)
+{
+    uint32_t L = wto_levels(sigma);
+    tree_t t;
+    int st = tree_init(&t, bits, n, L);
+    if (st) return st;
+    for (uint64_t q = 0; q < m; q++) {
+        uint64_t c = C[q], j = J[q];
+        if (c >= sigma || j == 0) { out[q] = UINT64_MAX; continue; }
+        uint64_t b = 0, e = n;
+        for (uint32_t l = 0; l < L; l++) {
+            int bit = (int)((c >> (L - 1 - l)) & 1);
+            if (bit) { b = rank0(&t, l, n) + rank1(&t, l, b); e = rank0(&t, l, n) + rank1(&t, l, e); }
+            else { b = rank0(&t, l, b); e = rank0(&t, l, e); }
+        }
+        if (j > e - b) { out[q] = UINT64_MAX; continue; }
+        uint64_t pos = b + j - 1;
+        for (uint32_t l = L; l-- > 0;) {
+            int bit = (int)((c >> (L - 1 - l)) & 1);
+            pos = bit ? selectb(&t, l, 1, pos - rank0(&t, l, n) + 1) : selectb(&t, l, 0, pos + 1);
+        }
+        out[q] = pos;
+    }
+    tree_free(&t);
+    return WTO_OK;
 }

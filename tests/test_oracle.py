@@ -367,3 +367,96 @@ def test_merge_rejects_inconsistent_node_starts():
     hx[-1] = 5  # does not end at the part's length
     with pytest.raises(O.OracleError):
         O.merge_bits([sorted_bits(S, 4)], [4], [hx], 4)
+
+
+# ---------------------------------------------------------------- wavelet matrix
+
+def wm_order(S, sigma, l):
+    """S_l of the wavelet matrix by numpy's stable sort on the reversed top l
+    bits (the last partition bit is the most significant key)."""
+    L = O.levels(sigma)
+    x = S.astype(np.uint64)
+    key = np.zeros(len(S), np.uint64)
+    for t in range(l):
+        key |= ((x >> np.uint64(L - 1 - t)) & np.uint64(1)) << np.uint64(t)
+    return S[np.argsort(key, kind="stable")]
+
+
+@pytest.mark.parametrize("sigma", [2, 3, 4, 5, 20, 96, 256, 300, 65536, (1 << 20) + 3])
+def test_matrix_levels_from_library_sort(sigma):
+    """B_l[p] = bit L-1-l of S_l, S_l from numpy's stable argsort; padding zero."""
+    rng = np.random.default_rng(sigma)
+    n = 3001
+    S = rng.integers(0, sigma, n).astype(inputs.sym_dtype(sigma))
+    L = O.levels(sigma)
+    bits = O.wm_bits(S, sigma)
+    assert bits.shape == (L, ((n + 511) // 512) * 64)
+    for l in range(L):
+        P = wm_order(S, sigma, l).astype(np.uint64)
+        want = ((P >> np.uint64(L - 1 - l)) & np.uint64(1)).astype(np.uint8)
+        full = np.unpackbits(bits[l], bitorder="little")
+        assert np.array_equal(full[:n], want), l
+        assert not full[n:].any()
+
+
+def test_matrix_small_worked_case():
+    """S = 3 0 2 1 3 3 0 over 4 codes, by hand: level 0 holds the high bits
+    1010110; S_1 = 0 1 0 3 2 3 3 (zeros of level 0 first) holds the low bits
+    0101011."""
+    S = np.array([3, 0, 2, 1, 3, 3, 0], np.uint8)
+    b = np.unpackbits(O.wm_bits(S, 4), axis=1, bitorder="little")[:, :7]
+    assert b[0].tolist() == [1, 0, 1, 0, 1, 1, 0]
+    assert b[1].tolist() == [0, 1, 0, 1, 0, 1, 1]
+
+
+def test_matrix_level_zero_and_sigma_two_equal_the_tree():
+    """Level 0 of both is the top-bit plane of S, and with one level the two coincide."""
+    S = inputs.zipf(4000, 96, 1.0, 3, np.uint8)
+    assert np.array_equal(O.wm_bits(S, 96)[0], O.build_bits(S, 96)[0])
+    T = inputs.uniform(4000, 2, 4, np.uint8)
+    assert np.array_equal(O.wm_bits(T, 2), O.build_bits(T, 2))
+
+
+@pytest.mark.parametrize("sigma", [2, 5, 20, 96, 256, 1000])
+def test_matrix_ones_per_level_match_histogram(sigma):
+    """Every level holds each symbol's bit once: ones_l = sum_c H[c] bit_l(c)."""
+    S = inputs.zipf(5000, sigma, 1.1, 9, inputs.sym_dtype(sigma))
+    L = O.levels(sigma)
+    H = np.bincount(S, minlength=sigma)
+    bits = O.wm_bits(S, sigma)
+    for l in range(L):
+        codes = np.arange(sigma)
+        want = int((H * ((codes >> (L - 1 - l)) & 1)).sum())
+        assert O.directory(bits[l], len(S))["ones"] == want
+
+
+@pytest.mark.parametrize("sigma,n", [(2, 50), (5, 200), (17, 300), (64, 257), (256, 513), (1000, 700)])
+def test_matrix_queries_against_brute_force(sigma, n):
+    """access = S[i], rank = count of c in [0, i), select = position of the
+    j-th c, all from S directly; sentinels for out-of-range arguments."""
+    rng = np.random.default_rng(n + sigma)
+    S = rng.integers(0, sigma, n).astype(inputs.sym_dtype(sigma))
+    bits = O.wm_bits(S, sigma)
+    I = np.arange(n + 2, dtype=np.uint64)
+    acc = O.wm_access(bits, n, sigma, I)
+    assert acc[:n].tolist() == S.tolist() and acc[n:].tolist() == [0xFFFFFFFF] * 2
+    cs = rng.integers(0, sigma + 1, 400).astype(np.uint32)
+    cs[: min(200, n)] = S[rng.integers(0, n, min(200, n))]
+    ii = rng.integers(0, n + 2, 400).astype(np.uint64)
+    want_r = [int((S[:i] == c).sum()) if (c < sigma and i <= n) else 2**64 - 1 for c, i in zip(cs, ii)]
+    assert O.wm_rank(bits, n, sigma, cs, ii).tolist() == want_r
+    jj = rng.integers(0, 12, 400).astype(np.uint64)
+    want_s = []
+    for c, j in zip(cs, jj):
+        pos = np.flatnonzero(S == c) if c < sigma else []
+        want_s.append(int(pos[j - 1]) if 1 <= j <= len(pos) else 2**64 - 1)
+    assert O.wm_select(bits, n, sigma, cs, jj).tolist() == want_s
+
+
+def test_matrix_sigma_one_has_no_levels():
+    S = np.zeros(10, np.uint8)
+    bits = O.wm_bits(S, 1)
+    assert bits.shape == (0, 64)
+    assert O.wm_access(bits, 10, 1, [0, 9, 10]).tolist() == [0, 0, 0xFFFFFFFF]
+    assert O.wm_rank(bits, 10, 1, [0, 0], [4, 10]).tolist() == [4, 10]
+    assert O.wm_select(bits, 10, 1, [0, 0], [1, 11]).tolist() == [0, 2**64 - 1]
