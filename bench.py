@@ -30,6 +30,9 @@ cont and rand): n = 2^30 four-byte codes over sigma = 2^y, y in {4, 6, ...,
 sequences: each built in 2^28-symbol chunks whose partial trees are then
 merged (wt_build_chunked), with the merge step's own bandwidth.
 
+``--workload matrix`` builds the wavelet matrices of the default sequences
+(the level-wise variant Section 5 names for future work).
+
 ``--impl reference`` times the CPU oracle instead (single thread, bounded
 sample of the same workload).  Under torchrun every rank builds its own
 replica (weak scaling, no collective on the data path); rank 0 prints.
@@ -576,6 +579,103 @@ def run_merge(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_matrix(args, ws, rank, local):
+    """Wavelet matrices of the default sequences (text and DNA, 2^30 symbols
+    each): a step builds both, device-resident; the same builds from pinned
+    host buffers end to end."""
+    import ctypes as C
+
+    import torch
+
+    from paper_1610_05994_gb300 import build as B
+    from paper_1610_05994_gb300 import wt as W
+
+    torch.cuda.set_device(local)
+    B.build_library()
+    lib = W.load()
+    dev = torch.device("cuda", local)
+    wls = WORKLOAD_SETS["text+dna"]
+    host = [w.generate(min(w.n, 1 << args.size_log2) if args.size_log2 else None) for w in wls]
+    sigmas = [w.sigma for w in wls]
+    seq_d = [torch.from_numpy(h).to(dev) for h in host]
+    torch.cuda.synchronize()
+
+    def step(keep):
+        trees = [W.Tree.build(S, sigma, wait=False, matrix=True) for S, sigma in zip(seq_d, sigmas)]
+        for t in keep:
+            t.free()
+        return trees
+
+    keep = []
+    for _ in range(args.warmup):
+        keep = step(keep)
+    for t in keep:
+        t.wait()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    W.profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        keep = step(keep)
+    e1.record()
+    torch.cuda.synchronize()
+    stats = W.profile_end()
+    clk = clocks.stop()
+    for t in keep:
+        t.wait()
+        t.free()
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, ws)
+    syms = sum(h.size for h in host)
+
+    host_p = [torch.from_numpy(h).pin_memory() for h in host]
+
+    def step_host(keep):
+        trees = []
+        for p, sigma in zip(host_p, sigmas):
+            h = lib.wt_build_matrix_async(C.c_void_p(p.data_ptr()), p.numel(), sigma, p.element_size(),
+                                          C.c_void_p(W._stream(None)))
+            if not h:
+                raise W.WTError(lib.wt_last_status(), "wt_build_matrix_async")
+            trees.append(W.Tree(h, p.numel(), sigma, p.element_size()))
+        for t in keep:
+            t.free()
+        return trees
+
+    keep = step_host([])
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    k2 = max(1, min(args.steps, 3))
+    f0.record()
+    for _ in range(k2):
+        keep = step_host(keep)
+    f1.record()
+    torch.cuda.synchronize()
+    for t in keep:
+        t.wait()
+        t.free()
+    ms_e2e = reduce_max(f0.elapsed_time(f1) / k2, ws)
+    if rank != 0:
+        return
+    roofline, kernels, launches = roofline_of(stats, args.steps)
+    line = {"metric": "wavelet-matrix build symbols/sec", "value": job_rate(syms, ws, ms), "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"wavelet matrices (Section 5, Claude and Navarro 2012): u8 text n={host[0].size} "
+                                   f"sigma=96 Zipf(1.0) + u8 DNA n={host[1].size} sigma=4 uniform, builds only",
+                       "parallelism": f"replicas{ws}", "l2": "inputs larger than L2; no flush"},
+            "roofline": roofline, "cpu_baseline": None,
+            "e2e": {"value": job_rate(syms, ws, ms_e2e), "unit": UNIT,
+                    "h2d_bytes_per_step": sum(h.nbytes for h in host), "d2h_bytes_per_step": 0,
+                    "ms_per_step": ms_e2e},
+            "gpu_launches": launches, "clocks": clk, "kernels": kernels}
+    print(json.dumps(line), flush=True)
+
+
 def roofline_of(stats: dict, steps: int):
     """Roofline of the kernel with the largest device time, per-kernel
     figures per step, and the number of library launches, from the library's
@@ -903,8 +1003,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + ["batch", "serve", "locality", "merge"],
-                    default="text+dna")
+    runners = {"batch": run_batch, "serve": run_serve, "locality": run_locality, "merge": run_merge,
+               "matrix": run_matrix}
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + sorted(runners), default="text+dna")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured build requests")
     ap.add_argument("--size-log2", type=int, default=0,
                     help="profiling aid: cap each sequence at 2^k symbols (the line then names the cap)")
@@ -913,7 +1014,7 @@ def main():
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
-        if args.workload in ("batch", "serve", "locality", "merge"):
+        if args.workload in runners:
             print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed on the single-sequence "
                               "workloads only"}), flush=True)
             return
@@ -923,9 +1024,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        {"batch": run_batch, "serve": run_serve, "locality": run_locality, "merge": run_merge}.get(
-            args.workload, run_ours)(
-            args, ws, rank, local)
+        runners.get(args.workload, run_ours)(args, ws, rank, local)
     finally:
         if ws > 1:
             import torch.distributed as dist

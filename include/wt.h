@@ -66,6 +66,9 @@ typedef enum {
  * not fit). */
 typedef enum { WT_VARIANT_AUTO = 0, WT_VARIANT_LEVELWISE = 1, WT_VARIANT_DD = 2 } wt_variant;
 
+/* What a handle holds (wt_info_t.layout). */
+typedef enum { WT_LAYOUT_TREE = 0, WT_LAYOUT_MATRIX = 1 } wt_layout;
+
 /* Query operation codes for wt_query_multi. */
 typedef enum { WT_OP_ACCESS = 0, WT_OP_RANK = 1, WT_OP_SELECT = 2 } wt_op;
 
@@ -98,6 +101,20 @@ wt_handle wt_build(const void *S, uint64_t n, uint64_t sigma, int sym_width);
  */
 wt_handle wt_build_async(const void *S, uint64_t n, uint64_t sigma, int sym_width, int variant,
                          void *stream);
+
+/*
+ * Builds the wavelet matrix of S[0..n) (the level-wise variant Section 5
+ * names for future work, as defined by Claude and Navarro 2012): level l
+ * holds bit L-1-l of every symbol of S_l, where S_0 = S and S_{l+1} is all
+ * of S_l stably partitioned by that bit, zeros first (one node per level).
+ * Levels use the layout above (bitmap, R, Hy, S1, S0, ones; Z_l = n - ones
+ * of level l).  Arguments, ownership, errors and staging of host symbols as
+ * wt_build_async.  wt_access, wt_rank and wt_select answer on the matrix
+ * (same conventions and sentinels as on a tree); wt_query_multi and
+ * wt_merge_async reject matrices with WT_ERR_ARG.  wt_info reports layout
+ * WT_LAYOUT_MATRIX.
+ */
+wt_handle wt_build_matrix_async(const void *S, uint64_t n, uint64_t sigma, int sym_width, void *stream);
 
 /* Waits for a handle's build to finish and returns its device-reported status. */
 wt_status wt_wait(wt_handle h);
@@ -194,7 +211,7 @@ typedef struct {
     uint32_t levels;      /* L */
     int32_t sym_width;
     int32_t variant;      /* the wt_variant that built it */
-    int32_t reserved;
+    int32_t layout;       /* wt_layout: a wavelet tree or a wavelet matrix */
     uint64_t device_bytes; /* resident bytes of the tree */
 } wt_info_t;
 

@@ -215,6 +215,7 @@ struct wt_tree {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     bool finalized = false;
+    bool matrix = false;  // a wavelet matrix (wt_build_matrix_async)
     wt_status status = WT_OK;
 };
 
@@ -373,6 +374,65 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
     return WT_OK;
 }
 
+// The wavelet matrix: the level-wise build with one node per level (node
+// tables OB_l = 0, ZE_l = Z_l from matrix.cu).  Level 0 is one node, so its
+// pass may hand level 1 its bitmap; deeper levels mix the top-bit keys in
+// every tile, so their count passes write the bitmaps from the symbols.
+wt_status enqueue_matrix(wt_tree *t, const void *S, cudaStream_t st) {
+    Scratch sc;
+    wt_status r = scratch_alloc(t->alloc, sc, t->n, t->sigma, t->L, t->width, true, st);
+    if (r != WT_OK) return r;
+    const BuildScratch &b = sc.b;
+    const double nw = (double)t->n * t->width;
+    const uint32_t R = hist_replicas(t->n, t->sigma);
+    const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
+    const bool fuse0 = !R && t->L > 0 && level0_fusable(S, t->n, t->width, t->sigma);
+    const bool next0 = t->L > 1 && pass_writes_next_bits(0, ntiles, t->width);
+    {
+        ProfScope p(K_HIST, nw, st);
+        if (R) {
+            WT_CK(launch_histogram_replicated(S, t->n, t->width, t->sigma, reinterpret_cast<uint32_t *>(b.hist), R,
+                                              t->d_err, st));
+        } else if (fuse0) {
+            const Level0Fuse z{t->h_desc.lv[0].words, b.cnt, next0 ? t->h_desc.lv[1].words : nullptr, t->L - 1};
+            WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st, &z));
+        } else {
+            WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st));
+        }
+    }
+    if (t->L > 0) {
+        const double leaves = (double)(1ull << t->L);
+        {
+            ProfScope p(K_NODE_STARTS, 8.0 * (t->sigma + leaves + 1), st);
+            if (R)
+                WT_CK(launch_node_starts_replicated(reinterpret_cast<const uint32_t *>(b.hist), R, t->sigma, t->L,
+                                                    b.hex, st, b.scan_tmp));
+            else
+                WT_CK(launch_node_starts(b.hist, t->sigma, t->L, t->n, b.hex, st, b.scan_tmp));
+        }
+        {
+            ProfScope p(K_NODE_TABLES, 8.0 * 3 * leaves, st);
+            WT_CK(launch_wm_tables(b.hex, t->L, b.ob, b.ze, st));
+        }
+        const void *cur = S;
+        void *bufs[2] = {b.ping, b.pong};
+        bool from_bits = false;
+        for (uint32_t l = 0; l < t->L; l++) {
+            void *nxt = (l + 1 < t->L) ? bufs[l & 1] : nullptr;
+            const bool next_bits = nxt && l == 0 && next0;
+            ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, nxt != nullptr), st);
+            WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
+                                    &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
+                                    next_bits ? t->h_desc.lv[l + 1].words : nullptr, t->d_err, b.job_slot, st,
+                                    l == 0 && fuse0));
+            from_bits = next_bits;
+            cur = nxt;
+        }
+    }
+    dev_free(t->alloc, sc.mem, sc.bytes, st);
+    return WT_OK;
+}
+
 // The dd-direct build (kernel d: per-tile counts, column scan, one write
 // pass over all levels) for small alphabets.
 wt_status enqueue_dd(wt_tree *t, const void *S, cudaStream_t st) {
@@ -447,6 +507,10 @@ wt_status enqueue_build(wt_tree *t, const void *S, int variant, cudaStream_t st)
             WT_CK(cudaMemsetAsync(t->h_desc.lv[l].Hy, 0, 8, st));
         }
         return WT_OK;
+    }
+    if (t->matrix) {
+        t->variant = WT_VARIANT_LEVELWISE;
+        return enqueue_matrix(t, S, st);
     }
     if (variant == WT_VARIANT_AUTO) variant = choose_variant(t->n, t->sigma, t->width);
     t->variant = variant;
@@ -905,7 +969,8 @@ cudaStream_t copy_stream() {
     return streams[dev];
 }
 
-wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int variant, cudaStream_t st) {
+wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int variant, cudaStream_t st,
+                      bool matrix = false) {
     wt_status r = check_args(S, n, sigma, width);
     if (r != WT_OK) {
         set_last(r);
@@ -927,6 +992,7 @@ wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int 
     t->width = width;
     t->stream = st;
     t->alloc = current_allocator();
+    t->matrix = matrix;
     if (cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         delete t;
@@ -1080,7 +1146,8 @@ wt_handle merge_async(const wt_handle *parts, uint32_t k, cudaStream_t st) {
     }
     uint64_t n = 0;
     for (uint32_t a = 0; a < k; a++) {
-        if (!parts[a] || parts[a]->sigma != parts[0]->sigma || parts[a]->width != parts[0]->width) {
+        if (!parts[a] || parts[a]->sigma != parts[0]->sigma || parts[a]->width != parts[0]->width ||
+            parts[a]->matrix) {
             set_last(WT_ERR_ARG);
             return nullptr;
         }
@@ -1205,6 +1272,10 @@ wt_status wt_build_batch(const void *const *S, const uint64_t *n, const uint64_t
     return set_last(build_batch_impl(S, n, sigma, sym_width, count, out, static_cast<cudaStream_t>(stream)));
 }
 
+wt_handle wt_build_matrix_async(const void *S, uint64_t n, uint64_t sigma, int sym_width, void *stream) {
+    return build_async(S, n, sigma, sym_width, WT_VARIANT_LEVELWISE, static_cast<cudaStream_t>(stream), true);
+}
+
 wt_handle wt_merge_async(const wt_handle *parts, uint32_t k, void *stream) {
     return merge_async(parts, k, static_cast<cudaStream_t>(stream));
 }
@@ -1216,7 +1287,9 @@ wt_handle wt_build_chunked(const void *S, uint64_t n, uint64_t sigma, int sym_wi
 wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, void *stream) {
     if (!h || (m && (!i || !out))) return set_last(WT_ERR_ARG);
     ProfScope p(K_Q_ACCESS, 16.0 * m, static_cast<cudaStream_t>(stream));
-    if (launch_access(h->d_desc, i, m, out, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    const cudaError_t e = h->matrix ? launch_wm_access(h->d_desc, i, m, out, static_cast<cudaStream_t>(stream))
+                                    : launch_access(h->d_desc, i, m, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return set_last(WT_ERR_CUDA);
     }
@@ -1226,7 +1299,9 @@ wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, v
 wt_status wt_rank(wt_handle h, const uint32_t *c, const uint64_t *i, uint64_t m, uint64_t *out, void *stream) {
     if (!h || (m && (!c || !i || !out))) return set_last(WT_ERR_ARG);
     ProfScope p(K_Q_RANK, 16.0 * m, static_cast<cudaStream_t>(stream));
-    if (launch_rank(h->d_desc, c, i, m, out, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    const cudaError_t e = h->matrix ? launch_wm_rank(h->d_desc, c, i, m, out, static_cast<cudaStream_t>(stream))
+                                    : launch_rank(h->d_desc, c, i, m, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return set_last(WT_ERR_CUDA);
     }
@@ -1236,7 +1311,9 @@ wt_status wt_rank(wt_handle h, const uint32_t *c, const uint64_t *i, uint64_t m,
 wt_status wt_select(wt_handle h, const uint32_t *c, const uint64_t *j, uint64_t m, uint64_t *out, void *stream) {
     if (!h || (m && (!c || !j || !out))) return set_last(WT_ERR_ARG);
     ProfScope p(K_Q_SELECT, 16.0 * m, static_cast<cudaStream_t>(stream));
-    if (launch_select(h->d_desc, c, j, m, out, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    const cudaError_t e = h->matrix ? launch_wm_select(h->d_desc, c, j, m, out, static_cast<cudaStream_t>(stream))
+                                    : launch_select(h->d_desc, c, j, m, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return set_last(WT_ERR_CUDA);
     }
@@ -1250,7 +1327,7 @@ wt_status wt_query_multi(const wt_handle *trees, uint32_t ntrees, const uint32_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::vector<const TreeDesc *> ptrs(ntrees);
     for (uint32_t k = 0; k < ntrees; k++) {
-        if (!trees[k]) return set_last(WT_ERR_ARG);
+        if (!trees[k] || trees[k]->matrix) return set_last(WT_ERR_ARG);
         ptrs[k] = trees[k]->d_desc;
     }
     const Allocator A = current_allocator();
@@ -1283,7 +1360,7 @@ wt_status wt_info(wt_handle h, wt_info_t *out) {
     out->levels = h->L;
     out->sym_width = h->width;
     out->variant = h->variant;
-    out->reserved = 0;
+    out->layout = h->matrix ? WT_LAYOUT_MATRIX : WT_LAYOUT_TREE;
     out->device_bytes = h->mem_bytes;
     return set_last(h->status);
 }

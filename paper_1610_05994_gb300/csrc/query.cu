@@ -17,52 +17,6 @@ namespace wt {
 
 constexpr int kQueryThreads = 256;
 
-__device__ __forceinline__ uint32_t bit_at(const LevelDesc &d, uint64_t p) {
-    return (__ldg(d.words + (p >> 5)) >> (p & 31)) & 1u;
-}
-
-// Position of the r-th (1-based) set bit of x; x holds at least r set bits.
-__device__ __forceinline__ uint32_t select_in_word(uint32_t x, uint32_t r) {
-    for (uint32_t k = 1; k < r; k++) x &= x - 1;
-    return __ffs(x) - 1;
-}
-
-// Position of the k-th (1-based) bit equal to `bit` on a level of n bits;
-// 1 <= k <= count of such bits below n.  The select sample of k bounds the
-// block from below, the next sample (if any) from above; a binary search on
-// the block directory and a scan of the block's 16 words finish it.
-__device__ uint64_t select_bit(const LevelDesc &d, uint64_t n, uint64_t nblocks, uint32_t bit, uint64_t k) {
-    const uint32_t *samples = bit ? d.S1 : d.S0;
-    const uint64_t count = bit ? d.ones : n - d.ones;
-    const uint64_t s = (k - 1) / kSample;
-    uint64_t lo = samples[s];
-    uint64_t hi = nblocks - 1;
-    if ((s + 1) * kSample < count) {
-        const uint64_t nx = samples[s + 1];
-        if (nx < hi) hi = nx;
-    }
-    // Largest block b in [lo, hi] with (bits equal to `bit` before b) < k.
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi + 1) >> 1;
-        const uint64_t ob = ones_before_block(d, mid);
-        const uint64_t before = bit ? ob : (mid << 9) - ob;
-        if (before < k)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const uint64_t ob = ones_before_block(d, lo);
-    uint64_t need = k - (bit ? ob : (lo << 9) - ob);
-    const uint32_t *w = d.words + lo * 16;
-    for (uint32_t q = 0; q < 16; q++) {
-        const uint32_t x = bit ? __ldg(w + q) : ~__ldg(w + q);
-        const uint32_t c = __popc(x);
-        if (need <= c) return (lo << 9) + q * 32 + select_in_word(x, (uint32_t)need);
-        need -= c;
-    }
-    return UINT64_MAX;  // unreachable for valid k
-}
-
 // One level step of the walk: returns the new p and narrows [b, e).
 __device__ __forceinline__ void descend(const LevelDesc &d, uint32_t bit, uint64_t &b, uint64_t &e, uint64_t &p) {
     const uint64_t rb = rank1(d, b), re = rank1(d, e), rp = rank1(d, p);

@@ -53,8 +53,8 @@ __host__ __device__ inline uint32_t levels_of(uint64_t sigma) {
     return L;
 }
 
-// ------------------------------------------------------- rank on a level
-// (query.cu, merge.cu)
+// ------------------------------------------------------- rank and select on a level
+// (query.cu, merge.cu, matrix.cu)
 
 // ones in B[0, 512 b): hyper entry plus the wrapped 32-bit block entry.
 __device__ __forceinline__ uint64_t ones_before_block(const LevelDesc &d, uint64_t b) {
@@ -86,6 +86,52 @@ __device__ __forceinline__ uint64_t rank1(const LevelDesc &d, uint64_t i) {
         }
     }
     return r;
+}
+
+__device__ __forceinline__ uint32_t bit_at(const LevelDesc &d, uint64_t p) {
+    return (__ldg(d.words + (p >> 5)) >> (p & 31)) & 1u;
+}
+
+// Position of the r-th (1-based) set bit of x; x holds at least r set bits.
+__device__ __forceinline__ uint32_t select_in_word(uint32_t x, uint32_t r) {
+    for (uint32_t k = 1; k < r; k++) x &= x - 1;
+    return __ffs(x) - 1;
+}
+
+// Position of the k-th (1-based) bit equal to `bit` on a level of n bits;
+// 1 <= k <= count of such bits below n.  The select sample of k bounds the
+// block from below, the next sample (if any) from above; a binary search on
+// the block directory and a scan of the block's 16 words finish it.
+__device__ inline uint64_t select_bit(const LevelDesc &d, uint64_t n, uint64_t nblocks, uint32_t bit, uint64_t k) {
+    const uint32_t *samples = bit ? d.S1 : d.S0;
+    const uint64_t count = bit ? d.ones : n - d.ones;
+    const uint64_t s = (k - 1) / kSample;
+    uint64_t lo = samples[s];
+    uint64_t hi = nblocks - 1;
+    if ((s + 1) * kSample < count) {
+        const uint64_t nx = samples[s + 1];
+        if (nx < hi) hi = nx;
+    }
+    // Largest block b in [lo, hi] with (bits equal to `bit` before b) < k.
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        const uint64_t ob = ones_before_block(d, mid);
+        const uint64_t before = bit ? ob : (mid << 9) - ob;
+        if (before < k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const uint64_t ob = ones_before_block(d, lo);
+    uint64_t need = k - (bit ? ob : (lo << 9) - ob);
+    const uint32_t *w = d.words + lo * 16;
+    for (uint32_t q = 0; q < 16; q++) {
+        const uint32_t x = bit ? __ldg(w + q) : ~__ldg(w + q);
+        const uint32_t c = __popc(x);
+        if (need <= c) return (lo << 9) + q * 32 + select_in_word(x, (uint32_t)need);
+        need -= c;
+    }
+    return UINT64_MAX;  // unreachable for valid k
 }
 
 // ------------------------------------------------------- TMA + mbarrier
@@ -359,6 +405,15 @@ cudaError_t launch_merge_starts(const TreeDesc *const *parts, uint32_t k, uint32
 cudaError_t launch_merge_level(const TreeDesc *const *parts, uint32_t k, uint32_t L, uint32_t l, const uint64_t *hex,
                                const uint64_t *hex_out, uint64_t n, uint32_t *words, uint32_t *err,
                                cudaStream_t st);
+
+// The wavelet matrix (matrix.cu): node tables OB_l = 0, ZE_l = Z_l for every
+// level from the leaf starts hex, and the matrix's queries.
+cudaError_t launch_wm_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, uint64_t *ze, cudaStream_t st);
+cudaError_t launch_wm_access(const TreeDesc *t, const uint64_t *i, uint64_t m, uint32_t *out, cudaStream_t st);
+cudaError_t launch_wm_rank(const TreeDesc *t, const uint32_t *c, const uint64_t *i, uint64_t m, uint64_t *out,
+                           cudaStream_t st);
+cudaError_t launch_wm_select(const TreeDesc *t, const uint32_t *c, const uint64_t *j, uint64_t m, uint64_t *out,
+                             cudaStream_t st);
 
 // Kernel (d): dd-direct build of all levels for small sigma (dd.cu).
 struct DdScratch {

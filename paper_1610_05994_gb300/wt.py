@@ -19,6 +19,7 @@ from . import build as _build
 OK, ERR_ARG, ERR_SYMBOL_RANGE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = range(6)
 VARIANT_AUTO, VARIANT_LEVELWISE, VARIANT_DD = 0, 1, 2
 OP_ACCESS, OP_RANK, OP_SELECT = 0, 1, 2
+LAYOUT_TREE, LAYOUT_MATRIX = 0, 1
 MAX_SIGMA = 1 << 28
 
 _lib = None
@@ -41,7 +42,7 @@ class _LevelView(C.Structure):
 
 class _Info(C.Structure):
     _fields_ = [("n", C.c_uint64), ("sigma", C.c_uint64), ("levels", C.c_uint32), ("sym_width", C.c_int32),
-                ("variant", C.c_int32), ("reserved", C.c_int32), ("device_bytes", C.c_uint64)]
+                ("variant", C.c_int32), ("layout", C.c_int32), ("device_bytes", C.c_uint64)]
 
 
 class _KernelStat(C.Structure):
@@ -59,6 +60,7 @@ _SIGNATURES = [
     ("wt_wait", C.c_int, [C.c_void_p]),
     ("wt_build_batch", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
                                  C.c_void_p]),
+    ("wt_build_matrix_async", C.c_void_p, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p]),
     ("wt_merge_async", C.c_void_p, [C.c_void_p, C.c_uint32, C.c_void_p]),
     ("wt_build_chunked", C.c_void_p, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_void_p]),
     ("wt_access", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
@@ -192,8 +194,10 @@ class Tree:
         return self._h.value
 
     @classmethod
-    def build(cls, S, sigma: int, variant: int = VARIANT_AUTO, stream=None, wait: bool = True) -> "Tree":
-        """Builds from a CUDA tensor or a numpy array of uint8/uint16/uint32 codes."""
+    def build(cls, S, sigma: int, variant: int = VARIANT_AUTO, stream=None, wait: bool = True,
+              matrix: bool = False) -> "Tree":
+        """Builds from a CUDA tensor or a numpy array of uint8/uint16/uint32
+        codes: the wavelet tree, or with matrix=True the wavelet matrix."""
         lib = load()
         if isinstance(S, np.ndarray):
             S = np.ascontiguousarray(S)
@@ -202,9 +206,12 @@ class Tree:
             if S.dtype not in (torch.uint8, torch.uint16, torch.uint32, torch.int32, torch.int16):
                 raise TypeError("symbols must be 8, 16 or 32-bit unsigned codes")
             width, ptr, n, keep = S.element_size(), _dptr(S), S.numel(), S
-        h = lib.wt_build_async(C.c_void_p(ptr), n, sigma, width, variant, C.c_void_p(_stream(stream)))
+        if matrix:
+            h = lib.wt_build_matrix_async(C.c_void_p(ptr), n, sigma, width, C.c_void_p(_stream(stream)))
+        else:
+            h = lib.wt_build_async(C.c_void_p(ptr), n, sigma, width, variant, C.c_void_p(_stream(stream)))
         if not h:
-            raise WTError(lib.wt_last_status(), "wt_build_async")
+            raise WTError(lib.wt_last_status(), "wt_build_matrix_async" if matrix else "wt_build_async")
         t = cls(h, n, sigma, width)
         t._keep = keep
         if wait or isinstance(S, np.ndarray):
@@ -231,7 +238,7 @@ class Tree:
         out = _Info()
         _check(load().wt_info(self._h, C.byref(out)), "wt_info")
         return {"n": out.n, "sigma": out.sigma, "levels": out.levels, "sym_width": out.sym_width,
-                "variant": out.variant, "device_bytes": out.device_bytes}
+                "variant": out.variant, "layout": out.layout, "device_bytes": out.device_bytes}
 
     def level(self, l: int) -> LevelView:
         """Copies of level l's bitmap words and directories (device tensors)."""
