@@ -375,9 +375,11 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
 }
 
 // The wavelet matrix: the level-wise build with one node per level (node
-// tables OB_l = 0, ZE_l = Z_l from matrix.cu).  Level 0 is one node, so its
-// pass may hand level 1 its bitmap; deeper levels mix the top-bit keys in
-// every tile, so their count passes write the bitmaps from the symbols.
+// tables OB_l = 0, ZE_l = Z_l from matrix.cu).  S_l is ordered by the
+// bit-reversed top l bits, so each top-l key is still one run of S_l and
+// most tiles take the pass's one-run path.  Only level 0's pass hands the
+// next level its bitmap; deeper count passes write the bitmaps from the
+// symbols.
 wt_status enqueue_matrix(wt_tree *t, const void *S, cudaStream_t st) {
     Scratch sc;
     wt_status r = scratch_alloc(t->alloc, sc, t->n, t->sigma, t->L, t->width, true, st);

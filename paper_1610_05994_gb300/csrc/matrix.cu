@@ -8,7 +8,9 @@
 // Z_l + ones_before(p).  The level step places bit 0 at zeros_before(p) +
 // OB_l[v] and bit 1 at ones_before(p) + ZE_l[v] for the symbol's top-l-bit
 // key v, so the matrix is built by the same count, scan and pass kernels
-// with node tables OB_l[v] = 0 and ZE_l[v] = Z_l for every v.  Those tables
+// with node tables OB_l[v] = 0 and ZE_l[v] = Z_l for every v (S_l is
+// ordered by the bit-reversed top l bits, so each key v is one run of S_l
+// and the pass's one-run path applies as on the tree).  Those tables
 // come from the leaf starts Hex: the codes whose bit L-1-l is zero form
 // 2^l runs of 2^(L-1-l) codes, and Z_l sums their counts.
 //
