@@ -58,3 +58,15 @@ def test_two_gloo_ranks(tmp_path):
     line = json.loads(r[0]["ref"].strip())
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+
+
+@pytest.mark.parametrize("workload", ["batch", "serve", "locality", "merge", "matrix"])
+def test_reference_arm_of_multi_sequence_workloads_is_unavailable(workload):
+    """The oracle is timed on the single-sequence workloads; the others print
+    one `unavailable` line and exit 0."""
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          workload], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "unavailable" in line
