@@ -49,6 +49,7 @@ def _load():
         lib.wto_level_order.argtypes = [vp, u64, i32, u64, u32, vp]
         lib.wto_build_bits.argtypes = [vp, u64, i32, u64, vp]
         lib.wto_pwt.argtypes = [vp, u64, i32, u64, vp]
+        lib.wto_pwt_level.argtypes = [vp, u64, i32, u64, u32, vp]
         lib.wto_dd.argtypes = [vp, u64, i32, u64, u32, vp]
         lib.wto_directory.argtypes = [vp, u64, vp, vp, vp, vp, vp, vp, vp]
         lib.wto_access.argtypes = [vp, u64, u64, vp, u64, vp]
@@ -127,6 +128,16 @@ def pwt_bits(S: np.ndarray, sigma: int) -> np.ndarray:
     L, lb = levels(sigma), level_bytes(len(S))
     out = np.zeros((L, lb), dtype=np.uint8)
     _check(_load().wto_pwt(_ptr(S), len(S), w, sigma, _ptr(out)))
+    return out
+
+
+def pwt_level_bits(S: np.ndarray, sigma: int, l: int) -> np.ndarray:
+    """Level l's bitmap alone, by Algorithm 1's per-level body (levels are
+    independent there, so long sequences can be checked level by level on
+    several host cores)."""
+    S, w = _seq(S)
+    out = np.zeros(level_bytes(len(S)), dtype=np.uint8)
+    _check(_load().wto_pwt_level(_ptr(S), len(S), w, sigma, l, _ptr(out)))
     return out
 
 

@@ -229,6 +229,26 @@ int wto_node_starts(const void *S, uint64_t n, int w, uint64_t sigma, uint64_t *
  * never materialises P_l; the tests use it as a second, independent route to
  * the same bitmaps.
  */
+/* One level i of Algorithm 1 over the codes x: counts per node, their
+ * exclusive prefix sum, then each symbol's bit at its node's running offset.
+ * B (wto_level_bytes(n) bytes) must be zero. */
+static int pwt_level(const uint32_t *x, uint64_t n, uint32_t L, uint32_t i, uint8_t *B)
+{
+    uint64_t nodes = 1ull << i;
+    uint64_t *C = (uint64_t *)calloc(nodes, sizeof(uint64_t));
+    if (!C) return WTO_ERR_NOMEM;
+    for (uint64_t j = 0; j < n; j++) C[node_of(x[j], L, i)]++;
+    uint64_t run = 0;                                   /* exclusive prefix sum */
+    for (uint64_t v = 0; v < nodes; v++) { uint64_t c = C[v]; C[v] = run; run += c; }
+    for (uint64_t j = 0; j < n; j++) {
+        uint64_t v = node_of(x[j], L, i);
+        bit_put(B, C[v], (x[j] & (1u << (L - i - 1))) != 0);
+        C[v]++;
+    }
+    free(C);
+    return WTO_OK;
+}
+
 int wto_pwt(const void *S, uint64_t n, int w, uint64_t sigma, uint8_t *bits)
 {
     uint32_t *x = NULL;
@@ -237,23 +257,28 @@ int wto_pwt(const void *S, uint64_t n, int w, uint64_t sigma, uint8_t *bits)
     uint32_t L = wto_levels(sigma);
     uint64_t lb = wto_level_bytes(n);
     memset(bits, 0, L * lb);
-    for (uint32_t i = 0; i < L; i++) {
-        uint64_t nodes = 1ull << i;
-        uint64_t *C = (uint64_t *)calloc(nodes, sizeof(uint64_t));
-        if (!C) { free(x); return WTO_ERR_NOMEM; }
-        for (uint64_t j = 0; j < n; j++) C[node_of(x[j], L, i)]++;
-        uint64_t run = 0;                               /* exclusive prefix sum */
-        for (uint64_t v = 0; v < nodes; v++) { uint64_t c = C[v]; C[v] = run; run += c; }
-        uint8_t *B = bits + i * lb;
-        for (uint64_t j = 0; j < n; j++) {
-            uint64_t v = node_of(x[j], L, i);
-            bit_put(B, C[v], (x[j] & (1u << (L - i - 1))) != 0);
-            C[v]++;
-        }
-        free(C);
-    }
+    for (uint32_t i = 0; i < L && st == WTO_OK; i++) st = pwt_level(x, n, L, i, bits + i * lb);
     free(x);
-    return WTO_OK;
+    return st;
+}
+
+/*
+ * Level i alone by Algorithm 1 (its per-level body; in Algorithm 1 the
+ * levels are independent, which is what pwt parallelises over): B receives
+ * wto_level_bytes(n) bytes.  Used to check very long sequences level by
+ * level on several host cores.
+ */
+int wto_pwt_level(const void *S, uint64_t n, int w, uint64_t sigma, uint32_t i, uint8_t *B)
+{
+    uint32_t L = wto_levels(sigma);
+    if (i >= L) return WTO_ERR_ARG;
+    uint32_t *x = NULL;
+    int st = load_codes(S, n, w, sigma, &x);
+    if (st) return st;
+    memset(B, 0, wto_level_bytes(n));
+    st = pwt_level(x, n, L, i, B);
+    free(x);
+    return st;
 }
 
 /*

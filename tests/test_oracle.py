@@ -152,6 +152,30 @@ def test_algorithm1_and_dd_agree_with_definition(sigma):
         assert np.array_equal(O.dd_bits(S, sigma, k), want), k
 
 
+@pytest.mark.parametrize("sigma", [2, 3, 16, 96, 65536, (1 << 20) + 3])
+def test_algorithm1_single_level_equals_library_sort(sigma):
+    """Level l alone (Algorithm 1's per-level body) is bit L-1-l of S stably
+    sorted by its top l bits, padding zero, for every l; out-of-range level
+    and symbol are errors."""
+    rng = np.random.default_rng(sigma + 3)
+    n = 5003
+    S = rng.integers(0, sigma, n).astype(inputs.sym_dtype(sigma))
+    L = O.levels(sigma)
+    for l in range(L):
+        P = stable_level_order(S, sigma, l).astype(np.uint64)
+        want = ((P >> np.uint64(L - 1 - l)) & np.uint64(1)).astype(np.uint8)
+        full = np.unpackbits(O.pwt_level_bits(S, sigma, l), bitorder="little")
+        assert np.array_equal(full[:n], want), l
+        assert not full[n:].any()
+    with pytest.raises(O.OracleError):
+        O.pwt_level_bits(S, sigma, L)
+    bad = S.copy()
+    bad[7] = sigma if sigma < (1 << (8 * bad.itemsize)) else 0
+    if bad[7] == sigma:
+        with pytest.raises(O.OracleError):
+            O.pwt_level_bits(bad, sigma, 0)
+
+
 def test_sigma_one_has_no_levels():
     S = np.zeros(100, dtype=np.uint8)
     assert O.levels(1) == 0
