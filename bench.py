@@ -384,7 +384,7 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype_of(args.workload), "data": "synthetic",
             "config": dict(config_for(args.workload), parallelism=f"replicas{ws}",
-                           variant={0: "auto", 1: "levelwise", 2: "dd"}[args.variant],
+                           variant={0: "auto", 1: "levelwise", 2: "dd", 3: "pairs"}[args.variant],
                            **({"reduced_size_log2": args.size_log2} if args.size_log2 else {})),
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": job_rate(syms_rank, ws, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -1009,8 +1009,8 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured build requests")
     ap.add_argument("--size-log2", type=int, default=0,
                     help="profiling aid: cap each sequence at 2^k symbols (the line then names the cap)")
-    ap.add_argument("--variant", type=int, choices=[0, 1, 2], default=0,
-                    help="0 auto (autotuned), 1 level-wise, 2 dd-direct")
+    ap.add_argument("--variant", type=int, choices=[0, 1, 2, 3], default=0,
+                    help="0 auto (autotuned), 1 level-wise, 2 dd-direct, 3 two levels per pass")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

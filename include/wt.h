@@ -60,11 +60,20 @@ typedef enum {
 } wt_status;
 
 /* Construction variants.  AUTO picks per (n, sigma, width) from a measured
- * table; LEVELWISE is the per-level pass (kernels a + b + c); DD builds every
+ * table; LEVELWISE is one level per pass (kernels a + b + c); DD builds every
  * level straight from S with per-tile prefix histograms (kernel d, for small
  * sigma only: it returns WT_ERR_ARG when 2^L - 1 node counters per tile do
- * not fit). */
-typedef enum { WT_VARIANT_AUTO = 0, WT_VARIANT_LEVELWISE = 1, WT_VARIANT_DD = 2 } wt_variant;
+ * not fit); PAIRS takes two levels per pass (a radix digit of two tree bits:
+ * one read of P_l writes levels l and l + 1 and places every symbol into
+ * P_{l+2}) for 1- and 2-byte symbols on levels whose tiles mostly lie in one
+ * node, and one level per pass elsewhere.  Every variant builds the same
+ * tree, bit for bit. */
+typedef enum {
+    WT_VARIANT_AUTO = 0,
+    WT_VARIANT_LEVELWISE = 1,
+    WT_VARIANT_DD = 2,
+    WT_VARIANT_PAIRS = 3
+} wt_variant;
 
 /* What a handle holds (wt_info_t.layout). */
 typedef enum { WT_LAYOUT_TREE = 0, WT_LAYOUT_MATRIX = 1 } wt_layout;
@@ -286,7 +295,12 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
  * every GPU that loads the library until the process exits.  Limits and
  * behaviour:
  *   - sigma must be at most 65536 (2^16); larger alphabets give WT_ERR_ARG
- *     (use wt_node_starts for them).  S must be device memory.
+ *     (use wt_node_starts for them).  S and Hex must be device memory of the
+ *     current device (else WT_ERR_ARG); the other argument rules are
+ *     wt_build's (a misaligned S gives WT_ERR_ARG before any launch).
+ *   - The array's address is cached per device for the life of the
+ *     process; after cudaDeviceReset on a device, do not call this entry
+ *     point on that device again.
  *   - The first call on a device looks up the array's device address on
  *     that device (with it current); make that first call before any stream
  *     capture.
@@ -307,9 +321,12 @@ wt_status wt_node_starts_noalloc(const void *S, uint64_t n, uint64_t sigma, int 
  * wt_profile_end waits for those events and writes one record per kernel
  * that ran (up to cap records to out; *count receives how many kernels
  * ran): launches (timed calls), the CUDA kernels those calls launched,
- * summed device time and summed algorithmic bytes (the bytes the method
- * must move for that launch: symbols read, bitmap and directory written,
- * next-level order written).
+ * summed device time and two summed byte counts.  alg_bytes is the
+ * level-wise method's byte model of the work the launch covers (per level:
+ * symbols read, bitmap and directory written, next-level order written; a
+ * step covering two levels counts both).  variant_bytes is what the
+ * launch's own variant must move (a two-level step reads the symbols once
+ * and writes the order two levels down).
  */
 typedef struct {
     char name[24];
@@ -317,6 +334,7 @@ typedef struct {
     uint64_t kernels;
     double total_ms;
     double alg_bytes;
+    double variant_bytes;
 } wt_kernel_stat_t;
 
 wt_status wt_profile_begin(void);

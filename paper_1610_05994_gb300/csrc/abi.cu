@@ -87,7 +87,8 @@ const char *kKernelNames[K_COUNT] = {"histogram",  "node_starts", "node_tables",
 
 struct ProfRecord {
     int kid;
-    double bytes;
+    double bytes;    // the level-wise byte model of what the launch covers
+    double vbytes;   // the bytes the launch's variant must move
     cudaEvent_t e0, e1;
     uint64_t k0, k1;  // kernel launch counter at the start and the end of the call
 };
@@ -121,10 +122,11 @@ struct ProfScope {
     int idx = -1;
     cudaStream_t st;
     unsigned flags = cudaEventRecordDefault;
-    ProfScope(int kid, double bytes, cudaStream_t s) : st(s) {
+    ProfScope(int kid, double bytes, cudaStream_t s) : ProfScope(kid, bytes, bytes, s) {}
+    ProfScope(int kid, double bytes, double vbytes, cudaStream_t s) : st(s) {
         std::lock_guard<std::mutex> lk(g_prof.mu);
         if (!g_prof.on) return;
-        ProfRecord r{kid, bytes, g_prof.take(), g_prof.take(), g_kernel_launches.load(), 0};
+        ProfRecord r{kid, bytes, vbytes, g_prof.take(), g_prof.take(), g_kernel_launches.load(), 0};
         if (!r.e0 || !r.e1) return;
         // Inside a stream capture the records become event nodes of the graph.
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -270,23 +272,62 @@ struct Scratch {
     void *mem = nullptr;
     size_t bytes = 0;
     BuildScratch b{};
+    uint32_t *plane[2] = {nullptr, nullptr};  // pair steps: bit l + 1 of P_l, packed like a bitmap
+    uint64_t *ptab = nullptr;                 // pair tables
 };
 
+// Which steps of a level-wise build take two levels in one pass: pair[l]
+// for a step covering levels l and l + 1.  A pair step needs 1- or 2-byte
+// symbols (its B split and hand-overs are those of the one-level pass's
+// byte path), a level l with at most 2^kPairMaxLevel nodes (its table) and,
+// like the one-level hand-over, few tiles spanning a node boundary of level
+// l (those place symbol by symbol).
+std::vector<uint8_t> level_schedule(uint64_t n, uint64_t sigma, uint32_t L, int width, bool pairs) {
+    std::vector<uint8_t> pair(L, 0);
+    if (!pairs || width > 2) return pair;
+    const uint64_t ntiles = ceil_div(n, lw_tile_elems(width));
+    for (uint32_t l = 0; l < L;) {
+        if (l + 1 < L && l <= kPairMaxLevel && pass_writes_next_bits(level_boundaries(n, sigma, l), ntiles, width)) {
+            pair[l] = 1;
+            l += 2;
+        } else {
+            l += 1;
+        }
+    }
+    return pair;
+}
+
+// Bytes a pair step must move (the variant's own model): read P_l, write
+// two levels' bitmaps and directories, and write P_{l+2} when a later pass
+// reads it.
+double pair_step_bytes(uint64_t n, int w, bool store) {
+    const double nw = (double)n * w;
+    return nw + 2 * (n / 8.0 + n / 128.0) + (store ? nw : 0.0);
+}
+
+// pair_lmax: the deepest level whose pair step splits into P_{l+2} (needs a
+// pair table), or -1 when no step does; pairs: some step is a pair step.
 wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t sigma, uint32_t L, int width,
-                        bool need_levels, cudaStream_t st) {
+                        bool need_levels, cudaStream_t st, bool pairs = false, int pair_lmax = -1) {
     const uint64_t ntiles = ceil_div(n, lw_tile_elems(width));
     const uint32_t R = hist_replicas(n, sigma);
     const size_t hist = align256(R ? (size_t)R * sigma * 4 : sigma * 8);
     const size_t hex = align256(((1ull << L) + 1) * 8);
     const size_t tab = need_levels ? align256((1ull << L) * 8) : 0;
-    const size_t counts = need_levels ? align256(lw_counts_bytes(n, width)) : 0;
-    const size_t prefix = need_levels ? align256(lw_prefix_bytes(n, width)) : 0;
+    // A pair step keeps three count arrays (and their prefixes), way w at w * stride.
+    const uint64_t units = lw_counts_bytes(n, width) / 4;
+    const size_t counts = need_levels ? align256(pairs ? 3 * way_cnt_stride(units) * 4 : lw_counts_bytes(n, width)) : 0;
+    const size_t prefix =
+        need_levels ? align256(pairs ? 3 * way_pre_stride(units) * 8 : lw_prefix_bytes(n, width)) : 0;
     const size_t zeroed = hist;
     const size_t buf = align256(n * (uint64_t)width);
     const size_t stmp = align256(scan_tmp_bytes(L));
-    const size_t jslot = level_job_slot_bytes();
+    const size_t jslot = std::max(level_job_slot_bytes(), pairs ? pair_job_slot_bytes() : (size_t)0);
     const int nbuf = need_levels ? (L >= 3 ? 2 : (L == 2 ? 1 : 0)) : 0;
-    sc.bytes = zeroed + counts + prefix + hex + 2 * tab + stmp + jslot + nbuf * buf;
+    // Two bit planes (bit l + 1 of P_l, read and written in turn) and the pair tables.
+    const size_t plane = pairs ? align256(ceil_div(n, kBlockBits) * 64) : 0;
+    const size_t ptab = pair_lmax >= 0 ? align256(pair_table_bytes((uint32_t)pair_lmax)) : 0;
+    sc.bytes = zeroed + counts + prefix + hex + 2 * tab + stmp + jslot + nbuf * buf + 2 * plane + ptab;
     sc.mem = dev_alloc(A, sc.bytes, st);
     if (!sc.mem) return WT_ERR_OOM;
     char *p = static_cast<char *>(sc.mem);
@@ -309,32 +350,63 @@ wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t si
     sc.b.ping = nbuf >= 1 ? p : nullptr;
     p += nbuf >= 1 ? buf : 0;
     sc.b.pong = nbuf >= 2 ? p : nullptr;
+    p += nbuf >= 2 ? buf : 0;
+    sc.plane[0] = plane ? reinterpret_cast<uint32_t *>(p) : nullptr;
+    p += plane;
+    sc.plane[1] = plane ? reinterpret_cast<uint32_t *>(p) : nullptr;
+    p += plane;
+    sc.ptab = ptab ? reinterpret_cast<uint64_t *>(p) : nullptr;
     WT_CK(cudaMemsetAsync(sc.mem, 0, zeroed, st));
     return WT_OK;
 }
 
 // The level-wise build (kernels a, a', then b + c per level) of a tree whose
-// memory is allocated, from device symbols S.
-wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
+// memory is allocated, from device symbols S.  pairs: take two levels per
+// pass where the schedule allows (level_schedule).
+wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pairs) {
+    const std::vector<uint8_t> pair = level_schedule(t->n, t->sigma, t->L, t->width, pairs);
+    int pair_lmax = -1;
+    uint32_t table_levels = 0;
+    bool any_pair = false;
+    for (uint32_t l = 0; l < t->L; l++)
+        if (pair[l]) {
+            any_pair = true;
+            if (l + 2 < t->L) {
+                pair_lmax = (int)l;
+                table_levels |= 1u << l;
+            }
+        }
     Scratch sc;
-    wt_status r = scratch_alloc(t->alloc, sc, t->n, t->sigma, t->L, t->width, true, st);
+    wt_status r = scratch_alloc(t->alloc, sc, t->n, t->sigma, t->L, t->width, true, st, any_pair, pair_lmax);
     if (r != WT_OK) return r;
     const BuildScratch &b = sc.b;
     const double nw = (double)t->n * t->width;
     const uint32_t R = hist_replicas(t->n, t->sigma);
     const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
+    const uint64_t units = lw_counts_bytes(t->n, t->width) / 4;
+    LevelDesc *lv = t->h_desc.lv;
     // Level 0's count pass rides on the histogram's read of S where it can
-    // (1-byte symbols): level 0's bitmap and unit counts, and level 1's
-    // bitmap zeroed when level 0's pass will write it.
+    // (1-byte symbols): level 0's bitmap and unit counts, and the bitmaps
+    // the first step ORs into zeroed.  For a pair step at level 0 also bit
+    // L - 2 of S and the counts of groups 01 and 11.
     const bool fuse0 = !R && t->L > 0 && level0_fusable(S, t->n, t->width, t->sigma);
+    const bool pair0 = t->L > 0 && pair[0];
     const bool next0 = t->L > 1 && pass_writes_next_bits(level_boundaries(t->n, t->sigma, 0), ntiles, t->width);
     {
-        ProfScope p(K_HIST, nw, st);
+        ProfScope p(K_HIST, nw, nw, st);
         if (R) {
             WT_CK(launch_histogram_replicated(S, t->n, t->width, t->sigma, reinterpret_cast<uint32_t *>(b.hist), R,
                                               t->d_err, st));
+        } else if (fuse0 && pair0) {
+            Level0Fuse z{lv[0].words, b.cnt, lv[1].words, t->L - 1};
+            z.plane = sc.plane[0];
+            z.cnt01 = b.cnt + way_cnt_stride(units);
+            z.cnt11 = b.cnt + 2 * way_cnt_stride(units);
+            z.next2 = 2 < t->L ? lv[2].words : nullptr;
+            z.plane3 = (3 < t->L && pair[2]) ? sc.plane[1] : nullptr;
+            WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st, &z));
         } else if (fuse0) {
-            const Level0Fuse z{t->h_desc.lv[0].words, b.cnt, next0 ? t->h_desc.lv[1].words : nullptr, t->L - 1};
+            const Level0Fuse z{lv[0].words, b.cnt, next0 ? lv[1].words : nullptr, t->L - 1};
             WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st, &z));
         } else {
             WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st));
@@ -343,7 +415,7 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
     if (t->L > 0) {
         const double leaves = (double)(1ull << t->L);
         {
-            ProfScope p(K_NODE_STARTS, 8.0 * (t->sigma + leaves + 1), st);
+            ProfScope p(K_NODE_STARTS, 8.0 * (t->sigma + leaves + 1), 8.0 * (t->sigma + leaves + 1), st);
             if (R)
                 WT_CK(launch_node_starts_replicated(reinterpret_cast<const uint32_t *>(b.hist), R, t->sigma, t->L,
                                                     b.hex, st, b.scan_tmp));
@@ -351,23 +423,73 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st) {
                 WT_CK(launch_node_starts(b.hist, t->sigma, t->L, t->n, b.hex, st, b.scan_tmp));
         }
         {
-            ProfScope p(K_NODE_TABLES, 8.0 * 5 * leaves, st);
+            ProfScope p(K_NODE_TABLES, 8.0 * 5 * leaves, 8.0 * 5 * leaves, st);
             WT_CK(launch_node_tables(b.hex, t->L, b.ob, b.ze, st, b.scan_tmp));
+            WT_CK(launch_pair_tables(b.hex, t->L, table_levels, sc.ptab, st));
         }
         const void *cur = S;
         void *bufs[2] = {b.ping, b.pong};
-        bool from_bits = false;  // level l's bitmap was written by the pass of level l - 1
-        for (uint32_t l = 0; l < t->L; l++) {
-            void *nxt = (l + 1 < t->L) ? bufs[l & 1] : nullptr;
-            const bool next_bits =
-                nxt && pass_writes_next_bits(level_boundaries(t->n, t->sigma, l), ntiles, t->width);
-            ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, nxt != nullptr), st);
-            WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
-                                    &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
-                                    next_bits ? t->h_desc.lv[l + 1].words : nullptr, t->d_err, b.job_slot, st,
-                                    l == 0 && fuse0));
-            from_bits = next_bits;
-            cur = nxt;
+        int bi = 0, pi = 0;
+        bool from_bits = false;  // level l's bitmap was written by the step before
+        bool plane_ok = false;   // and bit l + 1 of P_l is in sc.plane[pi]
+        for (uint32_t l = 0; l < t->L;) {
+            if (pair[l]) {
+                const bool need_b = l + 2 < t->L;
+                const bool store = l + 3 < t->L;  // a pass at level l + 2 reads P_{l+2}
+                const bool pnext = need_b && pair[l + 2];
+                PairJob j{};
+                j.cur = cur;
+                j.nxt = store ? bufs[bi] : nullptr;
+                j.n = t->n;
+                j.nblocks = ceil_div(t->n, kBlockBits);
+                j.L = t->L;
+                j.ntiles = (uint32_t)ntiles;
+                j.words = lv[l].words;
+                j.plane = sc.plane[pi];
+                j.next1 = lv[l + 1].words;
+                j.next2 = need_b ? lv[l + 2].words : nullptr;
+                j.plane3 = pnext ? sc.plane[pi ^ 1] : nullptr;
+                j.ob = b.ob + ((1ull << l) - 1);
+                j.ze = b.ze + ((1ull << l) - 1);
+                j.T = need_b ? sc.ptab + pair_table_offset(l) : nullptr;
+                j.cnt = b.cnt;
+                j.pre = b.pre;
+                j.need_b = need_b ? 1u : 0u;
+                ProfScope p(K_LEVEL_PASS,
+                            level_step_bytes(t->n, t->width, true) + level_step_bytes(t->n, t->width, l + 2 < t->L),
+                            pair_step_bytes(t->n, t->width, store), st);
+                WT_CK(launch_pair_step(j, t->width, l, lv[l], &t->d_desc->lv[l].ones, lv[l + 1],
+                                       &t->d_desc->lv[l + 1].ones, from_bits && plane_ok, l == 0 && fuse0, b.cnt,
+                                       b.pre, t->d_err, b.job_slot, st));
+                from_bits = need_b;
+                plane_ok = pnext;
+                if (pnext) pi ^= 1;
+                if (store) {
+                    cur = bufs[bi];
+                    bi ^= 1;
+                }
+                l += 2;
+            } else {
+                const bool has_next = l + 1 < t->L;
+                const bool next_bits =
+                    has_next && pass_writes_next_bits(level_boundaries(t->n, t->sigma, l), ntiles, t->width);
+                // The last level needs no symbols when its bitmap is handed over.
+                const bool store = has_next && !(l + 2 == t->L && next_bits);
+                void *nxt = store ? bufs[bi] : nullptr;
+                const double vb = nw + t->n / 8.0 + t->n / 128.0 + (store ? nw : 0.0);
+                ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, has_next), vb, st);
+                WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, lv[l],
+                                        &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
+                                        next_bits ? lv[l + 1].words : nullptr, t->d_err, b.job_slot, st,
+                                        l == 0 && fuse0));
+                from_bits = next_bits;
+                plane_ok = false;
+                if (store) {
+                    cur = bufs[bi];
+                    bi ^= 1;
+                }
+                l += 1;
+            }
         }
     }
     dev_free(t->alloc, sc.mem, sc.bytes, st);
@@ -486,15 +608,29 @@ wt_status enqueue_dd(wt_tree *t, const void *S, cudaStream_t st) {
     return r;
 }
 
-// Variant choice, from the measured table g_dd_faster: dd-direct where it
-// applies (one byte per symbol, sigma <= 256, n < 2^32) and was measured
-// faster than the level-wise build for that number of levels on GB300 (text
-// and DNA workloads of 2^28 symbols); level-wise otherwise.
+// Variant choice (AUTO), from measurements on GB300:
+//  * dd-direct where it applies (one byte per symbol, sigma <= 256,
+//    n < 2^32) and g_dd_faster says it beat the level-wise build for that
+//    number of levels;
+//  * two levels per pass where g_pairs_faster says so for the symbol width;
+//  * otherwise one level per pass.
+// The level step is bound by the ALU pipe (integer issue), not by HBM: a
+// pair step spends two byte splits per symbol plus three bit extractions,
+// about what two one-level steps spend, so it has not been faster
+// (2^28-symbol text: 25.7 ALU thread-instructions per symbol for a pair
+// step against 2 x 10.3 for two one-level steps).
 constexpr bool g_dd_faster[9] = {false, false, false, false, false, false, false, false, false};  // by L
+constexpr bool g_pairs_faster[3] = {false, false, false};                                      // by width 1, 2, 4
 
 int choose_variant(uint64_t n, uint64_t sigma, int width) {
     const uint32_t L = levels_of(sigma);
-    return (dd_supported(n, sigma, width) && L <= 8 && g_dd_faster[L]) ? WT_VARIANT_DD : WT_VARIANT_LEVELWISE;
+    if (dd_supported(n, sigma, width) && L <= 8 && g_dd_faster[L]) return WT_VARIANT_DD;
+    if (g_pairs_faster[width == 1 ? 0 : (width == 2 ? 1 : 2)]) {
+        const std::vector<uint8_t> pair = level_schedule(n, sigma, L, width, true);
+        for (uint8_t p : pair)
+            if (p) return WT_VARIANT_PAIRS;
+    }
+    return WT_VARIANT_LEVELWISE;
 }
 
 wt_status enqueue_build(wt_tree *t, const void *S, int variant, cudaStream_t st) {
@@ -517,7 +653,7 @@ wt_status enqueue_build(wt_tree *t, const void *S, int variant, cudaStream_t st)
     if (variant == WT_VARIANT_AUTO) variant = choose_variant(t->n, t->sigma, t->width);
     t->variant = variant;
     if (variant == WT_VARIANT_DD) return enqueue_dd(t, S, st);
-    return enqueue_levelwise(t, S, st);
+    return enqueue_levelwise(t, S, st, variant == WT_VARIANT_PAIRS);
 }
 
 // Waits for the build, copies the per-level counts back and reads the error word.
@@ -978,7 +1114,7 @@ wt_handle build_async(const void *S, uint64_t n, uint64_t sigma, int width, int 
         set_last(r);
         return nullptr;
     }
-    if (variant < WT_VARIANT_AUTO || variant > WT_VARIANT_DD ||
+    if (variant < WT_VARIANT_AUTO || variant > WT_VARIANT_PAIRS ||
         (variant == WT_VARIANT_DD && n > 0 && levels_of(sigma) > 0 && !dd_supported(n, sigma, width))) {
         set_last(WT_ERR_ARG);
         return nullptr;
@@ -1238,6 +1374,10 @@ wt_handle build_chunked(const void *S, uint64_t n, uint64_t sigma, int width, ui
 namespace wt {
 void note_launches(uint32_t k) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
 
+wt_status check_symbol_args(const void *S, uint64_t n, uint64_t sigma, int width) {
+    return check_args(S, n, sigma, width);
+}
+
 // Sets the calling thread's last status (for entry points in other files).
 wt_status record_status(wt_status s) { return set_last(s); }
 }  // namespace wt
@@ -1422,6 +1562,7 @@ wt_status wt_profile_end(wt_kernel_stat_t *out, uint32_t cap, uint32_t *count) {
         acc[rec.kid].kernels += rec.k1 - rec.k0;
         acc[rec.kid].total_ms += ms;
         acc[rec.kid].alg_bytes += rec.bytes;
+        acc[rec.kid].variant_bytes += rec.vbytes;
         g_prof.pool.push_back(rec.e0);
         g_prof.pool.push_back(rec.e1);
     }

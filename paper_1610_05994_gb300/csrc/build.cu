@@ -39,12 +39,26 @@ __device__ __forceinline__ uint32_t byte_bits16(const uint4 q, uint32_t bsh) {
 
 // Level 0's count pass for vector k of S (16 symbols; the 32 lanes of a warp
 // hold the 32 vectors of one 512-symbol unit, all active together).
+// With z.plane (a pair step at level 0) also bit bsh - 1 of the symbols and
+// the unit counts of groups 01 and 11 (bits (L-1, L-2) of the symbol).
 __device__ __forceinline__ void level0_vector(const Level0Fuse &z, uint64_t k, const uint4 q) {
     const uint32_t hb = byte_bits16(q, z.bsh);
     reinterpret_cast<uint16_t *>(z.words)[k] = (uint16_t)hb;
     if (z.next) reinterpret_cast<uint16_t *>(z.next)[k] = 0;
     const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(hb));
     if ((threadIdx.x & 31) == 0) z.cnt[k / 32] = c;
+    if (z.plane) {
+        const uint32_t hp = byte_bits16(q, z.bsh - 1);
+        reinterpret_cast<uint16_t *>(z.plane)[k] = (uint16_t)hp;
+        if (z.next2) reinterpret_cast<uint16_t *>(z.next2)[k] = 0;
+        if (z.plane3) reinterpret_cast<uint16_t *>(z.plane3)[k] = 0;
+        const uint32_t c01 = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(~hb & hp));
+        const uint32_t c11 = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(hb & hp));
+        if ((threadIdx.x & 31) == 0) {
+            z.cnt01[k / 32] = c01;
+            z.cnt11[k / 32] = c11;
+        }
+    }
 }
 
 // Whole tiles only: the level step's scan reads every unit count of every

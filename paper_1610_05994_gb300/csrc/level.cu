@@ -52,44 +52,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "wt_internal.cuh"
+#include "level_common.cuh"
 
 namespace wt {
-
-constexpr int kLwThreads = 256;
-constexpr int kLwWarps = kLwThreads / 32;
-constexpr int kLwSteps = 2;                                        // 512-byte warp steps per warp
-constexpr uint32_t kLwWarpBytes = 512 * kLwSteps;                  // a warp's range of the tile
-constexpr uint32_t kLwTileBytes = kLwWarpBytes * kLwWarps;         // 8 KB
-// Two runs, each starting at its destination's offset in a 32-symbol word
-// of the next bitmap, plus the reads of whole 32-symbol groups (4-byte
-// symbols: 2048 + 124 symbols at most).
-constexpr uint32_t kLwSplitBytes = kLwTileBytes + 512;
-constexpr int kLwStages = 4;
-constexpr uint32_t kLwStageBits = kLwTileBytes / 8;                 // a stage's copy of the level's bitmap (bytes)
-constexpr uint32_t kNoTile = 0xffffffffu;
-// The counts and prefixes are kept per unit of P_l: a warp's range or a rank
-// block of the bitmap, whichever is shorter (kLwWarpBytes or 512 symbols).
-// Every warp of the pass then reads the ones before its own range, and the
-// prefix scan reads the ones before every rank block, which is the rank
-// directory itself.
-constexpr uint32_t lw_unit_bytes(uint32_t width) { return 512 * width < kLwWarpBytes ? 512 * width : kLwWarpBytes; }
-constexpr uint32_t lw_units(uint32_t width) { return kLwTileBytes / lw_unit_bytes(width); }  // per tile
-constexpr uint32_t kLwMaxUnits = lw_units(1);
-
-template <typename Sym>
-struct LwCfg {
-    static constexpr int kW = (int)sizeof(Sym);
-    static constexpr int kSps = 16 / kW;                              // symbols per 16-byte chunk
-    static constexpr uint32_t kTile = kLwTileBytes / kW;              // symbols per tile
-    static constexpr uint32_t kBlocks = kTile / 512;                  // rank blocks per tile
-    static constexpr int kMinCtas = 4;                                // resident CTAs per SM
-    static constexpr uint32_t kUnits = lw_units(sizeof(Sym));         // count units per tile
-    static constexpr uint32_t kUnitsPerWarp = kLwWarpBytes / lw_unit_bytes(sizeof(Sym));
-    static constexpr uint32_t kPreCopy = kUnits + 2;                  // prefixes copied per tile
-};
-
-constexpr uint32_t kScanSeg = 4096;  // units per segment of the prefix scan
 
 uint32_t lw_tile_elems(int width) { return kLwTileBytes / (uint32_t)width; }
 size_t lw_counts_bytes(uint64_t n, int width) {
@@ -100,95 +65,6 @@ size_t lw_counts_bytes(uint64_t n, int width) {
 size_t lw_prefix_bytes(uint64_t n, int width) {
     const uint64_t nc = ceil_div(n, lw_tile_elems(width)) * lw_units((uint32_t)width);
     return (size_t)(nc + 2 + ceil_div(nc, kScanSeg) + 1) * 8;
-}
-
-struct LevelLaunch {
-    const LevelJob *jobs;        // device array of njobs
-    const uint32_t *tile_start;  // device, njobs + 1: first global tile of each job
-    uint32_t njobs, total_tiles, l;
-    uint32_t segs;               // scan segments of the largest job
-    uint32_t units, upb;         // count units per tile and per rank block
-    uint32_t *err;
-};
-
-// Job of global tile t: the largest k with tile_start[k] <= t.
-__device__ __forceinline__ uint32_t find_job(const LevelLaunch &a, uint32_t t) {
-    uint32_t lo = 0, hi = a.njobs - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (a.tile_start[mid] <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// The bits at shift `bsh` of the symbols of one 16-byte chunk, packed: bit k
-// = the chunk's symbol k.  Per 32-bit word the bit is first moved to the top
-// of each symbol's slot; for bytes one multiply then gathers the four top
-// bits into a nibble (its partial products meet only in bits 28..31).
-template <typename Sym>
-__device__ __forceinline__ uint32_t chunk_bits(const uint32_t (&x)[4], uint32_t bsh) {
-    uint32_t h = 0;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        if (sizeof(Sym) == 1) h |= ((((x[q] << (7 - bsh)) & 0x80808080u) * 0x00204081u) >> 28) << (4 * q);
-        if (sizeof(Sym) == 2) {
-            const uint32_t m = (x[q] << (15 - bsh)) & 0x80008000u;
-            h |= (((m >> 15) | (m >> 30)) & 3u) << (2 * q);
-        }
-        if (sizeof(Sym) == 4) h |= ((x[q] >> bsh) & 1u) << q;
-    }
-    return h;
-}
-
-template <typename Sym>
-__device__ __forceinline__ uint32_t sym_at(const uint32_t (&x)[4], int k) {
-    if (sizeof(Sym) == 1) return (x[k >> 2] >> (8 * (k & 3))) & 0xffu;
-    if (sizeof(Sym) == 2) return (x[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-    return x[k];
-}
-
-__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane, uint32_t &total) {
-    uint32_t inc = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += y;
-    }
-    total = __shfl_sync(0xffffffffu, inc, 31);
-    return inc - v;
-}
-
-__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-// Writes one run of the split copy to global memory: bytes [g0, g0 + len)
-// of the destination, held in shared memory at s (s and g0 agree modulo 16).
-// rt == 0 sends the 16-byte-aligned interior with one bulk store; rt in
-// [0, 32) (the caller's thread index relative to the run) writes the ragged
-// head (< 16 bytes) and tail (< 16 bytes).
-__device__ __forceinline__ void store_run(uintptr_t g0, uint32_t len, const unsigned char *s, int rt) {
-    if (len == 0) return;
-    const uintptr_t g1 = g0 + len;
-    const uintptr_t a = (g0 + 15) & ~(uintptr_t)15, b = g1 & ~(uintptr_t)15;
-    const uintptr_t head_end = a < g1 ? a : g1;
-    if (rt == 0 && b > a) bulk_store(reinterpret_cast<void *>(a), s + (a - g0), (uint32_t)(b - a));
-    if (rt < 16) {
-        const uintptr_t x = g0 + rt;
-        if (x < head_end) *reinterpret_cast<unsigned char *>(x) = s[x - g0];
-    } else if (rt < 32) {
-        const uintptr_t t0 = b > head_end ? b : head_end;
-        const uintptr_t x = t0 + (rt - 16);
-        if (x < g1) *reinterpret_cast<unsigned char *>(x) = s[x - g0];
-    }
 }
 
 // ---------------------------------------------------------------- counts
@@ -316,18 +192,22 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
 // two launches over segments of kScanSeg units (CTA x = job * segs + seg):
 // the sums of the segments, then each segment's scan from the sums of the
 // segments before it.
+// With a.ways = 3 (a pair step) blockIdx.y picks the count array; only way 0
+// (the level-l ones) writes the directory.
 __global__ void __launch_bounds__(1024) scan_sums_kernel(LevelLaunch a) {
     __shared__ uint32_t part[32];
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
     const LevelJob &J = a.jobs[job];
     const uint32_t nt = J.ntiles * a.units;  // units
     if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) return;
+    const uint32_t *cnt = J.cnt + blockIdx.y * way_cnt_stride(nt);
+    uint64_t *pre = J.pre + blockIdx.y * way_pre_stride(nt);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t c = 0;
 #pragma unroll
     for (int r = 0; r < (int)(kScanSeg / 1024); r++) {
         const uint32_t t = seg * kScanSeg + r * 1024 + tid;
-        if (t < nt) c += J.cnt[t];
+        if (t < nt) c += cnt[t];
     }
     c = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0) part[warp] = c;
@@ -335,7 +215,7 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(LevelLaunch a) {
     if (warp == 0) {
         uint32_t v = part[lane];
         v = __reduce_add_sync(0xffffffffu, v);
-        if (lane == 0) J.pre[nt + 2 + seg] = v;
+        if (lane == 0) pre[nt + 2 + seg] = v;
     }
 }
 
@@ -346,10 +226,13 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     const LevelJob &J = a.jobs[job];
     const uint32_t nt = J.ntiles * a.units;  // units
     if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) return;
+    const uint32_t way = blockIdx.y;
+    const uint32_t *cnt = J.cnt + way * way_cnt_stride(nt);
+    uint64_t *pre = J.pre + way * way_pre_stride(nt);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (warp == 0) {
         uint64_t b = 0;
-        for (uint32_t s2 = lane; s2 < seg; s2 += 32) b += J.pre[nt + 2 + s2];
+        for (uint32_t s2 = lane; s2 < seg; s2 += 32) b += pre[nt + 2 + s2];
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
         if (lane == 0) s_base = b;
@@ -358,7 +241,7 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     const uint32_t t0 = seg * kScanSeg + 4 * tid;
     uint32_t c[4];
 #pragma unroll
-    for (int j = 0; j < 4; j++) c[j] = t0 + j < nt ? J.cnt[t0 + j] : 0u;
+    for (int j = 0; j < 4; j++) c[j] = t0 + j < nt ? cnt[t0 + j] : 0u;
     const uint64_t sum = (uint64_t)c[0] + c[1] + c[2] + c[3];
     uint64_t inc = sum;
 #pragma unroll
@@ -388,9 +271,9 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     for (int j = 0; j < 4; j++) {
         const uint32_t t = t0 + j;
         if (t < nt) {
-            J.pre[t] = run;
+            pre[t] = run;
             const uint64_t b = t / upb;
-            if (t % upb == 0 && b < J.nblocks) {
+            if (way == 0 && t % upb == 0 && b < J.nblocks) {
                 const uint64_t next = run + c[j] + (upb == 2 && j + 1 < 4 ? c[j + 1] : 0u);
                 J.lv.R[b] = (uint32_t)run;
                 if ((b & kBlocksPerSpanMask) == 0) J.lv.Hy[b >> (kSpanShift - 9)] = run;
@@ -403,10 +286,12 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
         run += c[j];
     }
     if (t0 < nt && nt <= t0 + 4) {  // the total, read with the last tile's prefixes
-        J.pre[nt] = run;
-        J.lv.R[J.nblocks] = (uint32_t)run;
-        J.lv.Hy[J.nspans] = run;
-        *J.ones_out = run;
+        pre[nt] = run;
+        if (way == 0) {
+            J.lv.R[J.nblocks] = (uint32_t)run;
+            J.lv.Hy[J.nspans] = run;
+            *J.ones_out = run;
+        }
     }
 }
 
@@ -461,7 +346,10 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
     if (lane == 0) {
         const uint32_t tile = g - a.tile_start[k];
         const uint64_t base = (uint64_t)tile * Cfg::kTile;
-        const bool skip = S.J.nxt == nullptr;
+        // Nothing to place on a sequence's last level.  A pass with no next
+        // order to store (the next level is the last) still splits its tiles
+        // to hand that level its bitmap.
+        const bool skip = S.J.nxt == nullptr && S.J.next_words == nullptr;
         const bool full = !skip && S.J.n - base >= Cfg::kTile && (reinterpret_cast<uintptr_t>(S.J.cur) & 15) == 0;
         S.tile = tile;
         S.full = full;
@@ -486,6 +374,7 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
 // split copy: for a one-node tile its two runs.
 struct LwOut {
     bool runs;               // one node: a zeros run and a ones run
+    bool store;              // the runs go out to P_{l+1} (else only their next-level bits)
     uintptr_t gz_b, go_b;    // their destinations
     uint32_t zt, ones;       // their symbols
     uint32_t offz, B1;       // their places in the split copy (bytes)
@@ -560,8 +449,8 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
             bad = true;
         } else {
             runs = true;
-            gz_b = reinterpret_cast<uintptr_t>(nxt + gz);
-            go_b = reinterpret_cast<uintptr_t>(nxt + go);
+            gz_b = nxt ? reinterpret_cast<uintptr_t>(nxt + gz) : 0;
+            go_b = nxt ? reinterpret_cast<uintptr_t>(nxt + go) : 0;
             // Each run starts at its destination's offset within a 32-symbol
             // word of the next bitmap (which also agrees with the
             // destination modulo 16 bytes, as the bulk stores need).
@@ -617,7 +506,7 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                 } else {
                     const uint64_t dst = bit ? P + ob + __ldg(J.ze + v) : (base + p - P - ob) + __ldg(J.ob + v);
                     if (dst < J.n) {
-                        nxt[dst] = (Sym)sv;
+                        if (nxt) nxt[dst] = (Sym)sv;
                         if (next_words && ((sv >> (bsh - 1)) & 1u)) atomicOr(next_words + (dst >> 5), 1u << (dst & 31));
                     } else {
                         bad = true;
@@ -628,6 +517,7 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     }
     fence_proxy_async_smem();  // the split copy is read by bulk stores
     out.runs = runs;
+    out.store = nxt != nullptr;
     out.gz_b = gz_b;
     out.go_b = go_b;
     out.zt = Zt;
@@ -646,7 +536,7 @@ template <typename Sym>
 __device__ __forceinline__ void lw_store(const LwOut &o, const unsigned char *split) {
     constexpr uint32_t kW = sizeof(Sym);
     const int tid = threadIdx.x;
-    if (o.runs) {
+    if (o.runs && o.store) {
         if (tid < 32)
             store_run(o.gz_b, o.zt * kW, split + o.offz, tid);
         else if (tid < 64)
@@ -811,8 +701,9 @@ static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass,
             count_kernel<Sym, false><<<g0, kCountThreads, 0, st>>>(a);
         note_launches(1);
     }
-    scan_sums_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
-    scan_segs_kernel<<<a.njobs * a.segs, 1024, 0, st>>>(a);
+    const dim3 sg(a.njobs * a.segs, a.ways);
+    scan_sums_kernel<<<sg, 1024, 0, st>>>(a);
+    scan_segs_kernel<<<sg, 1024, 0, st>>>(a);
     note_launches(2);
     if (do_pass) {
         const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
@@ -835,8 +726,8 @@ LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint3
     j.ntiles = (uint32_t)ceil_div(n, lw_tile_elems(width));
     j.lv = lv;
     j.ones_out = ones_out;
-    j.ob = ob + ((1ull << l) - 1);
-    j.ze = ze + ((1ull << l) - 1);
+    j.ob = ob ? ob + ((1ull << l) - 1) : nullptr;
+    j.ze = ze ? ze + ((1ull << l) - 1) : nullptr;
     j.cnt = cnt;
     j.pre = pre;
     j.next_words = (l + 1 < L) ? next_words : nullptr;
@@ -857,12 +748,30 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.upb = width == 4 ? 2u : 1u;  // units per rank block: 512 symbols
     a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * a.units, kScanSeg);
     a.err = err;
+    a.ways = 1;
     switch (width) {
         case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, counted, st);
         case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, counted, st);
         case 4: return launch_lw<uint32_t>(a, from_bits, do_pass, counted, st);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_level_scans(int width, uint32_t l, const LevelJob *jobs, uint32_t njobs, uint32_t max_job_tiles,
+                               uint32_t ways, cudaStream_t st) {
+    LevelLaunch a{};
+    a.jobs = jobs;
+    a.njobs = njobs;
+    a.l = l;
+    a.units = lw_units((uint32_t)width);
+    a.upb = width == 4 ? 2u : 1u;
+    a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * a.units, kScanSeg);
+    a.ways = ways;
+    const dim3 sg(a.njobs * a.segs, a.ways);
+    scan_sums_kernel<<<sg, 1024, 0, st>>>(a);
+    scan_segs_kernel<<<sg, 1024, 0, st>>>(a);
+    note_launches(2);
+    return cudaGetLastError();
 }
 
 // Writes one job and its tile range to device memory (kernel parameters
@@ -876,6 +785,20 @@ __global__ void put_job_kernel(LevelJob j, LevelJob *dst, uint32_t *tile_start) 
 size_t level_job_bytes() { return sizeof(LevelJob); }
 
 size_t level_job_slot_bytes() { return (sizeof(LevelJob) + 2 * sizeof(uint32_t) + 255) & ~size_t(255); }
+
+cudaError_t launch_level_directory(uint64_t n, int width, uint32_t L, uint32_t l, LevelDesc lv, uint64_t *ones_out,
+                                   uint32_t *cnt, uint64_t *pre, uint32_t *err, void *job_slot, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    LevelJob j = make_level_job(nullptr, nullptr, n, width, L, l, nullptr, nullptr, lv, ones_out, cnt, pre, nullptr);
+    j.nxt = nullptr;
+    LevelJob *dj = static_cast<LevelJob *>(job_slot);
+    uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
+    put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, true, false, err, st, false);
+}
 
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,

@@ -1,0 +1,140 @@
+// level_common.cuh -- pieces shared by the level passes (level.cu: one
+// level per pass; pair.cu: two levels per pass): the tile geometry, the
+// launch record, bit extraction from 16-byte chunks of symbols and the bulk
+// stores of split runs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wt_internal.cuh"
+
+namespace wt {
+
+constexpr int kLwThreads = 256;
+constexpr int kLwWarps = kLwThreads / 32;
+constexpr int kLwSteps = 2;                                        // 512-byte warp steps per warp
+constexpr uint32_t kLwWarpBytes = 512 * kLwSteps;                  // a warp's range of the tile
+constexpr uint32_t kLwTileBytes = kLwWarpBytes * kLwWarps;         // 8 KB
+// Two runs, each starting at its destination's offset in a 32-symbol word
+// of the next bitmap, plus the reads of whole 32-symbol groups (4-byte
+// symbols: 2048 + 124 symbols at most).
+constexpr uint32_t kLwSplitBytes = kLwTileBytes + 512;
+constexpr int kLwStages = 4;
+constexpr uint32_t kLwStageBits = kLwTileBytes / 8;                 // a stage's copy of the level's bitmap (bytes)
+constexpr uint32_t kNoTile = 0xffffffffu;
+// The counts and prefixes are kept per unit of P_l: a warp's range or a rank
+// block of the bitmap, whichever is shorter (kLwWarpBytes or 512 symbols).
+// Every warp of the pass then reads the ones before its own range, and the
+// prefix scan reads the ones before every rank block, which is the rank
+// directory itself.
+constexpr uint32_t lw_unit_bytes(uint32_t width) { return 512 * width < kLwWarpBytes ? 512 * width : kLwWarpBytes; }
+constexpr uint32_t lw_units(uint32_t width) { return kLwTileBytes / lw_unit_bytes(width); }  // per tile
+constexpr uint32_t kLwMaxUnits = lw_units(1);
+
+template <typename Sym>
+struct LwCfg {
+    static constexpr int kW = (int)sizeof(Sym);
+    static constexpr int kSps = 16 / kW;                              // symbols per 16-byte chunk
+    static constexpr uint32_t kTile = kLwTileBytes / kW;              // symbols per tile
+    static constexpr uint32_t kBlocks = kTile / 512;                  // rank blocks per tile
+    static constexpr int kMinCtas = 4;                                // resident CTAs per SM
+    static constexpr uint32_t kUnits = lw_units(sizeof(Sym));         // count units per tile
+    static constexpr uint32_t kUnitsPerWarp = kLwWarpBytes / lw_unit_bytes(sizeof(Sym));
+    static constexpr uint32_t kPreCopy = kUnits + 2;                  // prefixes copied per tile
+};
+
+constexpr uint32_t kScanSeg = kScanSegUnits;
+
+
+struct LevelLaunch {
+    const LevelJob *jobs;        // device array of njobs
+    const uint32_t *tile_start;  // device, njobs + 1: first global tile of each job
+    uint32_t njobs, total_tiles, l;
+    uint32_t segs;               // scan segments of the largest job
+    uint32_t units, upb;         // count units per tile and per rank block
+    uint32_t *err;
+    uint32_t ways;               // count arrays the scan turns into prefixes (1, or 3 for a pair step)
+};
+
+// Job of global tile t: the largest k with tile_start[k] <= t.
+__device__ __forceinline__ uint32_t find_job(const LevelLaunch &a, uint32_t t) {
+    uint32_t lo = 0, hi = a.njobs - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (a.tile_start[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// The bits at shift `bsh` of the symbols of one 16-byte chunk, packed: bit k
+// = the chunk's symbol k.  Per 32-bit word the bit is first moved to the top
+// of each symbol's slot; for bytes one multiply then gathers the four top
+// bits into a nibble (its partial products meet only in bits 28..31).
+template <typename Sym>
+__device__ __forceinline__ uint32_t chunk_bits(const uint32_t (&x)[4], uint32_t bsh) {
+    uint32_t h = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (sizeof(Sym) == 1) h |= ((((x[q] << (7 - bsh)) & 0x80808080u) * 0x00204081u) >> 28) << (4 * q);
+        if (sizeof(Sym) == 2) {
+            const uint32_t m = (x[q] << (15 - bsh)) & 0x80008000u;
+            h |= (((m >> 15) | (m >> 30)) & 3u) << (2 * q);
+        }
+        if (sizeof(Sym) == 4) h |= ((x[q] >> bsh) & 1u) << q;
+    }
+    return h;
+}
+
+template <typename Sym>
+__device__ __forceinline__ uint32_t sym_at(const uint32_t (&x)[4], int k) {
+    if (sizeof(Sym) == 1) return (x[k >> 2] >> (8 * (k & 3))) & 0xffu;
+    if (sizeof(Sym) == 2) return (x[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+    return x[k];
+}
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane, uint32_t &total) {
+    uint32_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Writes one run of the split copy to global memory: bytes [g0, g0 + len)
+// of the destination, held in shared memory at s (s and g0 agree modulo 16).
+// rt == 0 sends the 16-byte-aligned interior with one bulk store; rt in
+// [0, 32) (the caller's thread index relative to the run) writes the ragged
+// head (< 16 bytes) and tail (< 16 bytes).
+__device__ __forceinline__ void store_run(uintptr_t g0, uint32_t len, const unsigned char *s, int rt) {
+    if (len == 0) return;
+    const uintptr_t g1 = g0 + len;
+    const uintptr_t a = (g0 + 15) & ~(uintptr_t)15, b = g1 & ~(uintptr_t)15;
+    const uintptr_t head_end = a < g1 ? a : g1;
+    if (rt == 0 && b > a) bulk_store(reinterpret_cast<void *>(a), s + (a - g0), (uint32_t)(b - a));
+    if (rt < 16) {
+        const uintptr_t x = g0 + rt;
+        if (x < head_end) *reinterpret_cast<unsigned char *>(x) = s[x - g0];
+    } else if (rt < 32) {
+        const uintptr_t t0 = b > head_end ? b : head_end;
+        const uintptr_t x = t0 + (rt - 16);
+        if (x < g1) *reinterpret_cast<unsigned char *>(x) = s[x - g0];
+    }
+}
+
+}  // namespace wt

@@ -34,7 +34,10 @@ std::mutex g_scratch_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device (looked up and cached
-// on the first call made with that device current).
+// on the first call made with that device current).  The cache is kept for
+// the life of the process: after cudaDeviceReset the device image, and with
+// it the array, is loaded anew, so a process that resets a device must not
+// call this entry point on it again.
 cudaError_t scratch_on_current_device(unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -55,23 +58,42 @@ cudaError_t scratch_on_current_device(unsigned char **out) {
 
 namespace wt {
 wt_status record_status(wt_status s);  // abi.cu: sets the calling thread's last status
+// abi.cu: the argument rules every build shares (width, sigma, S present
+// and naturally aligned, n below 2^56).
+wt_status check_symbol_args(const void *S, uint64_t n, uint64_t sigma, int width);
 }
+
+namespace {
+
+// Whether p is device memory of device dev (or managed memory).
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+}  // namespace
 
 extern "C" wt_status wt_node_starts_noalloc(const void *S, uint64_t n, uint64_t sigma, int sym_width, uint64_t *Hex,
                                             void *stream) {
     using namespace wt;
-    if (sym_width != 1 && sym_width != 2 && sym_width != 4) return record_status(WT_ERR_ARG);
-    if (sigma == 0 || sigma > kNoAllocMaxSigma) return record_status(WT_ERR_ARG);
-    if (sym_width < 4 && sigma > (1ull << (8 * sym_width))) return record_status(WT_ERR_ARG);
-    if (!Hex || (n > 0 && S == nullptr) || n >= (1ull << 56)) return record_status(WT_ERR_ARG);
-    if (n > 0) {
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, S) != cudaSuccess) {
-            cudaGetLastError();
-            return record_status(WT_ERR_ARG);
-        }
-        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return record_status(WT_ERR_ARG);
+    // The same rules as every build (so a misaligned S is refused here, on
+    // the host, before any launch), plus this entry point's own limit.
+    const wt_status ar = check_symbol_args(S, n, sigma, sym_width);
+    if (ar != WT_OK) return record_status(ar);
+    if (sigma > kNoAllocMaxSigma || !Hex) return record_status(WT_ERR_ARG);
+    // S and Hex must live on the current device: the scratch used is the
+    // current device's copy of the array.
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return record_status(WT_ERR_CUDA);
     }
+    if ((n > 0 && !on_device(S, dev)) || !on_device(Hex, dev)) return record_status(WT_ERR_ARG);
     unsigned char *scratch = nullptr;
     if (scratch_on_current_device(&scratch) != cudaSuccess) {
         cudaGetLastError();

@@ -312,9 +312,13 @@ struct BuildScratch {
 // bsh) of every symbol goes to level 0's bitmap (words), the ones of every
 // 512-symbol unit to cnt (the count pass's layout), and level 1's bitmap is
 // zeroed (next, when level 0's pass writes it; else nullptr).
+// For a pair step at level 0 it also writes bit L - 2 of every symbol to
+// plane, the unit counts of ways 1 and 2 to cnt01 and cnt11, and zeroes
+// next2 and plane3 (each when not nullptr).
 struct Level0Fuse {
     uint32_t *words, *cnt, *next;
     uint32_t bsh;
+    uint32_t *plane = nullptr, *cnt01 = nullptr, *cnt11 = nullptr, *next2 = nullptr, *plane3 = nullptr;
 };
 bool level0_fusable(const void *S, uint64_t n, int width, uint64_t sigma);
 cudaError_t launch_histogram(const void *S, uint64_t n, int width, uint64_t sigma, uint64_t *hist,
@@ -380,6 +384,59 @@ inline uint64_t level_boundaries(uint64_t n, uint64_t sigma, uint32_t l) {
 inline bool pass_writes_next_bits(uint64_t boundaries, uint64_t tiles, int width) {
     return width <= 2 && boundaries * 64 < tiles;
 }
+// ------------------------------------------------------- two levels per pass
+// (pair.cu) A pair step builds levels l and l + 1 with one read of P_l and
+// places every symbol straight into P_{l+2}.  Its count pass stores three
+// counts per unit of P_l: the level-l ones (way 0), the symbols with bits
+// (l, l + 1) = (0, 1) (way 1) and (1, 1) (way 2); the prefix scan turns each
+// into unit prefixes.  The ways live in one array each, way w at offset
+// w * stride.
+constexpr uint32_t kScanSegUnits = 4096;  // units per segment of the prefix scan
+__host__ __device__ inline uint64_t way_cnt_stride(uint64_t units) { return (units + 3) & ~3ull; }
+__host__ __device__ inline uint64_t way_pre_stride(uint64_t units) {
+    return (units + 2 + ceil_div(units, kScanSegUnits) + 1 + 1) & ~1ull;
+}
+
+// One sequence's share of a pair launch.  Bitmaps written here (next1,
+// next2, plane3) must be zero where this step does not store whole words:
+// the count pass zeroes them.
+struct __align__(16) PairJob {
+    const void *cur;           // P_l
+    void *nxt;                 // P_{l+2}; nullptr when no later pass reads it
+    uint64_t n, nblocks;
+    uint32_t L, ntiles;
+    uint32_t *words;           // level l's bitmap (the count pass writes it when it reads the symbols)
+    uint32_t *plane;           // bit l + 1 of P_l, packed like a bitmap
+    uint32_t *next1;           // level l + 1's bitmap
+    uint32_t *next2;           // level l + 2's bitmap, or nullptr
+    uint32_t *plane3;          // bit l + 3 of P_{l+2}, packed like a bitmap, or nullptr
+    const uint64_t *ob, *ze;   // level l's node tables
+    const uint64_t *T;         // level l's pair table (4 per node), nullptr when l + 2 = L
+    uint32_t *cnt;             // unit counts, three ways
+    uint64_t *pre;             // unit prefixes, three ways
+    uint32_t need_b;           // l + 2 < L: the symbols are split into their P_{l+2} runs
+    uint32_t pad;
+};
+// Pair table of level l: T[4 v + g] = C_{l+2}[4 v + g] - (symbols of group g
+// in the nodes before v), for every node v with 2^l <= kPairMaxNodes; a
+// symbol of group g at position p of P_l, in node v, goes to
+// T[4 v + g] + (symbols of group g in P_l[0, p)).  Level l's table starts at
+// entry pair_table_offset(l).
+constexpr uint32_t kPairMaxLevel = 16;
+inline uint64_t pair_table_offset(uint32_t l) { return 4 * ((1ull << l) - 1); }
+inline size_t pair_table_bytes(uint32_t lmax) { return 8 * 4 * ((1ull << (lmax + 1)) - 1); }
+// levels: bit l set for every level whose table is wanted (all l + 2 < L).
+cudaError_t launch_pair_tables(const uint64_t *hex, uint32_t L, uint32_t levels, uint64_t *T, cudaStream_t st);
+size_t pair_job_slot_bytes();
+// One pair step of one sequence (job_slot: pair_job_slot_bytes()): the
+// count pass (from_bits: from level l's bitmap and plane l + 1, else from
+// the symbols; counted: the counts are already in place), the three-way
+// prefix scan with level l's directory (lv, ones_out), the pair pass, then
+// level l + 1's directory from the bitmap the pass wrote (lv1, ones1_out).
+cudaError_t launch_pair_step(const PairJob &j, int width, uint32_t l, LevelDesc lv, uint64_t *ones_out,
+                             LevelDesc lv1, uint64_t *ones1_out, bool from_bits, bool counted, uint32_t *cnt1,
+                             uint64_t *pre1, uint32_t *err, void *job_slot, cudaStream_t st);
+
 // Level l of every job (all of one width): counts (from the symbols, which
 // also writes level l's bitmap, or from_bits: from that bitmap), prefix
 // scan with the rank directory, and (do_pass) the pass that places P_{l+1}.
@@ -394,6 +451,15 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
                               uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
                               cudaStream_t st, bool counted = false);
+
+// The prefix scan alone of level l (ways count arrays, way 0 with the
+// directory), over jobs already in device memory.
+cudaError_t launch_level_scans(int width, uint32_t l, const LevelJob *jobs, uint32_t njobs, uint32_t max_job_tiles,
+                               uint32_t ways, cudaStream_t st);
+// Level l's directory from its bitmap (already written): count from the
+// bitmap and the prefix scan, no pass.
+cudaError_t launch_level_directory(uint64_t n, int width, uint32_t L, uint32_t l, LevelDesc lv, uint64_t *ones_out,
+                                   uint32_t *cnt, uint64_t *pre, uint32_t *err, void *job_slot, cudaStream_t st);
 
 // Merge of partial trees (merge.cu).  parts: device array of k device
 // descriptors of trees with the same alphabet.  launch_merge_starts

@@ -35,6 +35,7 @@ class BuildRequest:
     admitted: float = 0.0
     done: float = 0.0
     n: int = 0
+    error: str | None = None  # why the request was rejected or its build failed
 
 
 @dataclass
@@ -69,6 +70,8 @@ class Server:
         self.resident: OrderedDict = OrderedDict()  # rid -> (tree, bytes, request)
         self.used = 0
         self.finished: list[BuildRequest] = []
+        self.failed: list[BuildRequest] = []     # builds whose wait raised (their bytes are given back)
+        self.rejected: list[BuildRequest] = []   # requests larger than the whole budget
         self.queries: list[QueryBatch] = []
         self.last_query_event: torch.cuda.Event | None = None
         self.evicted = 0
@@ -97,6 +100,14 @@ class Server:
         while self.queue and len(batch) < self.max_batch:
             req = self.queue[0]
             need = tree_bytes(req.S.numel(), req.sigma, req.S.element_size())
+            if need > self.budget:
+                # It can never fit: refuse it before evicting anything, so it
+                # neither empties the resident set nor blocks the queue.
+                self.queue.popleft()
+                req.error = f"needs {need} bytes, more than the {self.budget}-byte budget"
+                req.S = None
+                self.rejected.append(req)
+                continue
             while self.used + need > self.budget and self._evict_oldest():
                 pass
             if self.used + need > self.budget:
@@ -125,10 +136,20 @@ class Server:
                 continue
             now = time.perf_counter()
             for (req, need), tree in zip(batch, trees):
-                tree.wait()            # raises if this sequence failed
-                req.done = now
                 req.n = req.S.numel()
                 req.S = None           # the build no longer reads it
+                try:
+                    tree.wait()        # raises if this sequence failed
+                except W.WTError as e:
+                    # Record the failure, give back its bytes and go on
+                    # retiring the rest of the batch.
+                    req.error = str(e)
+                    self.failed.append(req)
+                    self.used -= need
+                    with torch.cuda.stream(self.build_stream):
+                        tree.free()
+                    continue
+                req.done = now
                 self.finished.append(req)
                 self.resident[req.rid] = (tree, need, req)
                 self.built_symbols += req.n

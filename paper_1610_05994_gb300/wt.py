@@ -17,7 +17,7 @@ import torch
 from . import build as _build
 
 OK, ERR_ARG, ERR_SYMBOL_RANGE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = range(6)
-VARIANT_AUTO, VARIANT_LEVELWISE, VARIANT_DD = 0, 1, 2
+VARIANT_AUTO, VARIANT_LEVELWISE, VARIANT_DD, VARIANT_PAIRS = 0, 1, 2, 3
 OP_ACCESS, OP_RANK, OP_SELECT = 0, 1, 2
 LAYOUT_TREE, LAYOUT_MATRIX = 0, 1
 MAX_SIGMA = 1 << 28
@@ -47,7 +47,7 @@ class _Info(C.Structure):
 
 class _KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_uint64), ("kernels", C.c_uint64), ("total_ms", C.c_double),
-                ("alg_bytes", C.c_double)]
+                ("alg_bytes", C.c_double), ("variant_bytes", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -359,7 +359,15 @@ def node_starts_noalloc(S: torch.Tensor, sigma: int, out: torch.Tensor | None = 
     memory (scratch in a fixed library array; sigma <= 2^16; calls must not
     overlap on the GPU)."""
     L = max(0, (sigma - 1).bit_length())
-    hex_ = torch.empty((1 << L) + 1, dtype=torch.uint64, device=S.device) if out is None else out
+    if out is None:
+        hex_ = torch.empty((1 << L) + 1, dtype=torch.uint64, device=S.device)
+    else:
+        # The library writes 2^L + 1 uint64 through the raw pointer.
+        if out.dtype != torch.uint64 or out.numel() < (1 << L) + 1 or out.device != S.device \
+                or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous uint64 tensor of at least {(1 << L) + 1} elements "
+                             f"on {S.device}")
+        hex_ = out
     _check(load().wt_node_starts_noalloc(C.c_void_p(_dptr(S)), S.numel(), sigma, S.element_size(),
                                          C.c_void_p(_dptr(hex_)), C.c_void_p(_stream(stream))),
            "wt_node_starts_noalloc")
@@ -391,5 +399,6 @@ def profile_end() -> dict:
     cnt = C.c_uint32()
     _check(load().wt_profile_end(arr, cap, C.byref(cnt)), "wt_profile_end")
     return {arr[k].name.decode(): {"launches": int(arr[k].launches), "kernels": int(arr[k].kernels),
-                                   "total_ms": float(arr[k].total_ms), "alg_bytes": float(arr[k].alg_bytes)}
+                                   "total_ms": float(arr[k].total_ms), "alg_bytes": float(arr[k].alg_bytes),
+                                   "variant_bytes": float(arr[k].variant_bytes)}
             for k in range(min(cnt.value, cap))}

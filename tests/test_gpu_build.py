@@ -13,7 +13,7 @@ pytestmark = [pytest.mark.gpu, needs_gpu]
 WORKLOAD_SMALL = inputs.WORKLOADS["u8-uniform-2^20-s256"]
 
 
-VARIANTS = [1, 2]  # level-wise (kernels a+b+c), dd-direct (kernel d)
+VARIANTS = [1, 2, 3]  # one level per pass (kernels a+b+c), dd-direct (kernel d), two levels per pass
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -26,12 +26,14 @@ def test_small_workload_bit_exact(variant):
     compare_tree(t, S, WORKLOAD_SMALL.sigma)
 
 
-def test_auto_variant_is_one_of_the_two_and_levelwise_for_wide_symbols():
+def test_auto_variant_is_a_concrete_variant_and_levelwise_for_wide_symbols():
     W = wt()
     a = W.Tree.build(to_dev(inputs.uniform(5000, 96, 1, np.uint8)), 96)
     b = W.Tree.build(to_dev(inputs.uniform(5000, 1000, 1, np.uint16)), 1000)
-    assert a.info()["variant"] in (W.VARIANT_DD, W.VARIANT_LEVELWISE)
-    assert b.info()["variant"] == W.VARIANT_LEVELWISE
+    c = W.Tree.build(to_dev(inputs.uniform(5000, 1000, 1, np.uint32)), 1000)
+    assert a.info()["variant"] in (W.VARIANT_DD, W.VARIANT_PAIRS, W.VARIANT_LEVELWISE)
+    assert b.info()["variant"] in (W.VARIANT_PAIRS, W.VARIANT_LEVELWISE)
+    assert c.info()["variant"] == W.VARIANT_LEVELWISE
 
 
 def test_dd_rejects_what_it_cannot_build():
@@ -57,13 +59,14 @@ def test_edge_shapes_u8(sigma, n, variant):
     compare_tree(t, S, sigma)
 
 
+@pytest.mark.parametrize("variant", [1, 3])
 @pytest.mark.parametrize("sigma,dtype", [(257, np.uint16), (1000, np.uint16), (65536, np.uint16),
                                          (4, np.uint32), (1 << 20, np.uint32), ((1 << 20) + 3, np.uint32)])
 @pytest.mark.parametrize("n", [1, 513, 2047, 2048, 2049, 4096, 4097, 70001])
-def test_wide_symbols(sigma, dtype, n):
+def test_wide_symbols(sigma, dtype, n, variant):
     W = wt()
     S = inputs.zipf(n, sigma, 1.2, 77 + n, dtype)
-    t = W.Tree.build(to_dev(S), sigma)
+    t = W.Tree.build(to_dev(S), sigma, variant=variant)
     compare_tree(t, S, sigma)
 
 
@@ -84,14 +87,18 @@ def test_level0_count_with_a_partial_last_tile_on_reused_memory(n):
         compare_tree(t, S, 96)
 
 
-def test_host_input_and_unaligned_device_input():
+@pytest.mark.parametrize("variant", [1, 3])
+def test_host_input_and_unaligned_device_input(variant):
     """S may be host memory; a device S that is not 16-byte aligned takes the scalar path."""
     W = wt()
     sigma = 96
     S = inputs.zipf(50001, sigma, 1.0, 5, np.uint8)
-    compare_tree(W.Tree.build(S, sigma), S, sigma)
+    compare_tree(W.Tree.build(S, sigma, variant=variant), S, sigma)
     D = to_dev(np.concatenate([np.zeros(3, np.uint8), S]))
-    compare_tree(W.Tree.build(D[3:], sigma), S, sigma)
+    compare_tree(W.Tree.build(D[3:], sigma, variant=variant), S, sigma)
+    S2 = inputs.zipf(70001, 1000, 1.1, 6, np.uint16)
+    D2 = to_dev(np.concatenate([np.zeros(1, np.uint16), S2]))
+    compare_tree(W.Tree.build(D2[1:], 1000, variant=variant), S2, 1000)
 
 
 def test_many_tiles_zipf_multi_level_scatter():
@@ -179,7 +186,9 @@ def test_async_build_on_stream_and_torch_allocator():
 
 @pytest.mark.parametrize("sigma,dtype,log2n,alpha,variant", [
     (96, np.uint8, 25, 1.0, 1), (4, np.uint8, 25, 0.0, 1), (96, np.uint8, 25, 1.0, 2), (4, np.uint8, 25, 0.0, 2),
-    (256, np.uint8, 24, 0.0, 2), (65536, np.uint16, 23, 1.1, 1), (1 << 20, np.uint32, 22, 1.2, 1)])
+    (256, np.uint8, 24, 0.0, 2), (65536, np.uint16, 23, 1.1, 1), (1 << 20, np.uint32, 22, 1.2, 1),
+    (96, np.uint8, 25, 1.0, 3), (4, np.uint8, 25, 0.0, 3), (256, np.uint8, 24, 0.0, 3), (20, np.uint8, 24, 1.1, 3),
+    (16, np.uint8, 25, 0.0, 3), (65536, np.uint16, 23, 1.1, 3), (4096, np.uint16, 24, 1.2, 3)])
 def test_many_tiles_per_cta_pipeline(sigma, dtype, log2n, alpha, variant):
     """Enough tiles that every persistent CTA streams several (the producer /
     compute pipeline runs at full depth), plus a ragged tail."""

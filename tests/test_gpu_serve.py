@@ -71,3 +71,36 @@ def test_serving_results_equal_alone():
     for rid, (tree, _, req) in list(srv.resident.items()):
         compare_tree(tree, seqs[rid], specs[rid].sigma, check_dir=False)
     srv.close()
+
+
+def test_failed_and_oversized_requests_do_not_stall_the_loop():
+    """A request larger than the whole budget is refused without evicting
+    anything; a build that fails (a symbol >= sigma) is recorded, its bytes
+    are given back, and the other builds of its batch still become resident
+    with trees equal to the oracle's."""
+    W = wt()
+    from paper_1610_05994_gb300.serve import BuildRequest, Server, tree_bytes
+    good = [inputs.zipf(5000 + 17 * k, 256, 1.0, 50 + k, np.uint8) for k in range(3)]
+    bad = inputs.uniform(6000, 200, 60, np.uint8)
+    bad[4321] = 250
+    huge = np.zeros(1 << 20, np.uint8)
+    budget = 6 * tree_bytes(len(bad) + 1000, 256, 1)   # room for all four small builds
+    assert tree_bytes(len(huge), 256, 1) > budget
+    srv = Server(budget_bytes=budget, max_batch=8)
+    srv.submit(BuildRequest(0, to_dev(good[0]), 256, 0.0))
+    srv.step()
+    srv.drain()
+    assert list(srv.resident) == [0]
+    srv.submit(BuildRequest(1, to_dev(huge), 256, 0.0))
+    srv.submit(BuildRequest(2, to_dev(good[1]), 256, 0.0))
+    srv.submit(BuildRequest(3, to_dev(bad), 200, 0.0))
+    srv.submit(BuildRequest(4, to_dev(good[2]), 256, 0.0))
+    srv.drain()
+    assert [r.rid for r in srv.rejected] == [1] and srv.rejected[0].error
+    assert [r.rid for r in srv.failed] == [3] and srv.failed[0].error
+    assert sorted(srv.resident) == [0, 2, 4]
+    assert srv.evicted == 0
+    assert srv.used == sum(v[1] for v in srv.resident.values())
+    for rid, S in ((0, good[0]), (2, good[1]), (4, good[2])):
+        compare_tree(srv.resident[rid][0], S, 256)
+    srv.close()
