@@ -26,7 +26,7 @@
 // bitmap word), and the count pass only popcounts it; otherwise the count
 // pass writes it from the symbols.  The last level therefore needs no pass.
 //
-// GPU structure of the pass: a persistent CTA of 256 threads takes a
+// GPU structure of the pass: a persistent CTA of 128 threads takes a
 // contiguous range of tiles and keeps four stages: the last warp claims a
 // tile three ahead and one thread issues TMA bulk copies (cp.async.bulk) of its
 // symbols, its unit prefixes and its slice of level l's bitmap into a
@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
                 // The lane's chunk of load r is 16 (8, 4) consecutive bits of
                 // the bitmap, at byte (base + (512 r + 16 lane) / w) / 8.
                 unsigned char *bl = bm + base / 8 + (16 * lane / sizeof(Sym)) / 8;
+                const BitGather gg = bit_gather<Sym>(bsh);
 #pragma unroll
                 for (int h = 0; h < kVecs; h += 4) {
                     uint4 w[4];
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
 #pragma unroll
                     for (int r = 0; r < 4; r++) {
                         const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
-                        const uint32_t hb = chunk_bits<Sym>(x, bsh);
+                        const uint32_t hb = gather_bits<Sym>(x, gg, bsh);
                         c[(h + r) / kPerUnit] += __popc(hb);
                         unsigned char *d = bl + (h + r) * (512 / sizeof(Sym) / 8);
                         if (sizeof(Sym) == 1) *reinterpret_cast<uint16_t *>(d) = (uint16_t)hb;
@@ -412,13 +413,15 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
 
     // Count: level bits of the lane's chunks (16, 8 or 4 consecutive bits of
     // the level's bitmap, copied into the stage), per-lane and per-warp ones.
-    uint32_t x[kLwSteps][4], h[kLwSteps];
-    uint32_t cpk = 0;  // step st's count in bits [16 st, 16 st + 16)
+    // The counts of two steps share a word (16 bits each) and one scan.
+    constexpr int kPk = (kLwSteps + 1) / 2;
+    uint32_t h[kLwSteps];
+    uint32_t cpk[kPk], lpk[kPk], tpk[kPk];
+#pragma unroll
+    for (int k2 = 0; k2 < kPk; k2++) cpk[k2] = 0;
 #pragma unroll
     for (int st = 0; st < kLwSteps; st++) {
         const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;  // the chunk's byte in the tile
-        const uint4 v = *reinterpret_cast<const uint4 *>(buf + q);
-        x[st][0] = v.x, x[st][1] = v.y, x[st][2] = v.z, x[st][3] = v.w;
         const uint32_t b0 = q / kW / 8;  // the chunk's first bitmap byte in the tile
         uint32_t hb = 0;
         if (kWhole || b0 < S.bits_bytes) {
@@ -427,10 +430,10 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
             if (kSps == 4) hb = (sbits[b0] >> (4 * (lane & 1))) & 15u;
         }
         h[st] = hb;
-        cpk += (uint32_t)__popc(h[st]) << (16 * st);
+        cpk[st >> 1] += (uint32_t)__popc(hb) << (16 * (st & 1));
     }
-    uint32_t tpk;
-    const uint32_t lpk = warp_excl_scan(cpk, lane, tpk);
+#pragma unroll
+    for (int k2 = 0; k2 < kPk; k2++) lpk[k2] = warp_excl_scan(cpk[k2], lane, tpk[k2]);
 
     // Placement.
     bool runs = false;
@@ -460,8 +463,11 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
 #pragma unroll
             for (int st = 0; st < kLwSteps; st++) {
                 const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;
-                const uint32_t o = wx + stx + ((lpk >> (16 * st)) & 0xffffu);  // ones before the chunk
-                stx += (tpk >> (16 * st)) & 0xffffu;
+                const uint32_t sh16 = 16 * (st & 1);
+                const uint32_t o = wx + stx + ((lpk[st >> 1] >> sh16) & 0xffffu);  // ones before the chunk
+                stx += (tpk[st >> 1] >> sh16) & 0xffffu;
+                const uint4 v = *reinterpret_cast<const uint4 *>(buf + q);
+                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
                 // A one goes to po; a zero to C + k kW - po (its zeros-before, scaled).
                 uint32_t po = B1 + o * kW;
                 const uint32_t C = offz + B1 + q;
@@ -470,7 +476,7 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                     if (kWhole || q / kW + kk < cnt) {
                         const bool one = (h[st] >> kk) & 1u;
                         const uint32_t at = one ? po : C + kk * kW - po;
-                        const uint32_t sv = sym_at<Sym>(x[st], kk);
+                        const uint32_t sv = sym_at<Sym>(x, kk);
                         if (kW == 1) split[at] = (unsigned char)sv;
                         if (kW == 2) *reinterpret_cast<uint16_t *>(split + at) = (uint16_t)sv;
                         if (kW == 4) *reinterpret_cast<uint32_t *>(split + at) = sv;
@@ -558,6 +564,7 @@ __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char
     const uint32_t nwz = o.zt ? ((uint32_t)(o.gz & 31) + o.zt + 31) / 32 : 0u;
     const uint32_t nwo = o.ones ? ((uint32_t)(o.go & 31) + o.ones + 31) / 32 : 0u;
     const uint32_t zbase = 0, obase = o.B1 - (uint32_t)(o.go & 31) * kW;  // group 0 of each run
+    const BitGather gg = bit_gather<Sym>(o.bsh_next);
     for (uint32_t t = threadIdx.x; t < nwz + nwo; t += kLwThreads) {
         const bool zr = t < nwz;
         const uint32_t k = zr ? t : t - nwz;
@@ -567,7 +574,7 @@ __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char
         for (uint32_t c = 0; c < kW * 2; c++) {
             const uint4 v = *reinterpret_cast<const uint4 *>(g + 16 * c);
             const uint32_t x[4] = {v.x, v.y, v.z, v.w};
-            bits |= chunk_bits<Sym>(x, o.bsh_next) << (c * (16 / kW));
+            bits |= gather_bits<Sym>(x, gg, o.bsh_next) << (c * (16 / kW));
         }
         const uint32_t first = (uint32_t)((zr ? o.gz : o.go) & 31);   // the run's first bit in word 0
         const uint32_t len = zr ? o.zt : o.ones;
@@ -745,7 +752,7 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.total_tiles = total_tiles;
     a.l = l;
     a.units = lw_units((uint32_t)width);
-    a.upb = width == 4 ? 2u : 1u;  // units per rank block: 512 symbols
+    a.upb = 512u * (uint32_t)width / lw_unit_bytes((uint32_t)width);  // units per rank block of 512 symbols
     a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * a.units, kScanSeg);
     a.err = err;
     a.ways = 1;
@@ -764,7 +771,7 @@ cudaError_t launch_level_scans(int width, uint32_t l, const LevelJob *jobs, uint
     a.njobs = njobs;
     a.l = l;
     a.units = lw_units((uint32_t)width);
-    a.upb = width == 4 ? 2u : 1u;
+    a.upb = 512u * (uint32_t)width / lw_unit_bytes((uint32_t)width);
     a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * a.units, kScanSeg);
     a.ways = ways;
     const dim3 sg(a.njobs * a.segs, a.ways);

@@ -11,9 +11,9 @@
 
 namespace wt {
 
-constexpr int kLwThreads = 256;
+constexpr int kLwThreads = 128;
 constexpr int kLwWarps = kLwThreads / 32;
-constexpr int kLwSteps = 2;                                        // 512-byte warp steps per warp
+constexpr int kLwSteps = 4;                                        // 512-byte warp steps per warp
 constexpr uint32_t kLwWarpBytes = 512 * kLwSteps;                  // a warp's range of the tile
 constexpr uint32_t kLwTileBytes = kLwWarpBytes * kLwWarps;         // 8 KB
 // Two runs, each starting at its destination's offset in a 32-symbol word
@@ -87,6 +87,39 @@ __device__ __forceinline__ uint32_t chunk_bits(const uint32_t (&x)[4], uint32_t 
         if (sizeof(Sym) == 4) h |= ((x[q] >> bsh) & 1u) << q;
     }
     return h;
+}
+
+// The same bits gathered with one AND and one 64-bit multiply per 8 bytes
+// (the multiply runs on the FMA pipe, which the passes leave mostly idle,
+// where chunk_bits spends shifts and masks on the ALU pipe).  For bytes the
+// AND keeps bit bsh of each byte j at 8 j + bsh; the multiplier (the sum of
+// 2^(7 k + 7 - bsh), k = 0..7) moves it to bit 56 + j, every other partial
+// product lands on a distinct bit below 56 or beyond 63, so nothing carries
+// into the top byte.  For 2-byte symbols the same with 2^(15 k + 15 - bsh),
+// k = 0..3, and the top nibble.
+struct BitGather {
+    uint64_t mask, mul;
+};
+template <typename Sym>
+__device__ __forceinline__ BitGather bit_gather(uint32_t bsh) {
+    BitGather g;
+    if (sizeof(Sym) == 1) {
+        g.mask = 0x0101010101010101ull << bsh;
+        g.mul = 0x0102040810204080ull >> bsh;
+    } else {
+        g.mask = 0x0001000100010001ull << bsh;
+        g.mul = ((1ull << 15) | (1ull << 30) | (1ull << 45) | (1ull << 60)) >> bsh;
+    }
+    return g;
+}
+template <typename Sym>
+__device__ __forceinline__ uint32_t gather_bits(const uint32_t (&x)[4], const BitGather &g, uint32_t bsh) {
+    if (sizeof(Sym) == 4) return chunk_bits<Sym>(x, bsh);
+    const uint64_t lo = ((uint64_t)x[1] << 32) | x[0], hi = ((uint64_t)x[3] << 32) | x[2];
+    constexpr int kTop = sizeof(Sym) == 1 ? 56 : 60, kPer = sizeof(Sym) == 1 ? 8 : 4;
+    const uint32_t a = (uint32_t)(((lo & g.mask) * g.mul) >> kTop);
+    const uint32_t b = (uint32_t)(((hi & g.mask) * g.mul) >> kTop);
+    return a | (b << kPer);
 }
 
 template <typename Sym>

@@ -21,7 +21,7 @@
 // and bit l + 3 of P_{l+2}, so that the next pair step's counts read bits,
 // not symbols.
 //
-// GPU structure: the one-level pass's persistent CTA (256 threads, tiles of
+// GPU structure: the one-level pass's persistent CTA (128 threads, tiles of
 // 8 KB, TMA bulk copies of the symbols, level l's bitmap, bit l + 1 of P_l
 // and the unit prefixes into three stages claimed by the last warp).  Per
 // tile in one node of level l:
@@ -45,6 +45,10 @@ namespace {
 
 constexpr int kPairStages = 3;
 constexpr uint32_t kPairBBytes = kLwTileBytes + 1024;  // four runs at their destinations' offsets in 32-symbol words
+// Batches of kLwThreads 32-symbol groups of A a tile can need: the two runs
+// of a tile of 8192 bytes span at most 8192 / 32 + 4 groups of 1-byte
+// symbols (fewer for wider symbols).
+constexpr int kGB = (int)((kLwTileBytes / 32 + 4 + kLwThreads - 1) / kLwThreads);
 
 struct PairLaunch {
     const PairJob *jobs;          // device array of njobs
@@ -139,6 +143,7 @@ __global__ void __launch_bounds__(256, 4) pair_count_kernel(PairLaunch a) {
             if (cnt == Cfg::kTile && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
                 const uint4 *v = reinterpret_cast<const uint4 *>(S + base) + lane;
                 const size_t boff = base / 8 + (16 * lane / sizeof(Sym)) / 8;
+                const BitGather g0 = bit_gather<Sym>(bsh), g1 = bit_gather<Sym>(bsh - 1);
                 uint32_t a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
                 for (int h = 0; h < kVecs; h += 4) {
@@ -148,8 +153,8 @@ __global__ void __launch_bounds__(256, 4) pair_count_kernel(PairLaunch a) {
 #pragma unroll
                     for (int r = 0; r < 4; r++) {
                         const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
-                        const uint32_t hb = chunk_bits<Sym>(x, bsh);
-                        const uint32_t hp = chunk_bits<Sym>(x, bsh - 1);
+                        const uint32_t hb = gather_bits<Sym>(x, g0, bsh);
+                        const uint32_t hp = gather_bits<Sym>(x, g1, bsh - 1);
                         a0 += __popc(hb);
                         a1 += __popc(~hb & hp);
                         a2 += __popc(hb & hp);
@@ -257,7 +262,7 @@ struct PairShared {
     PairJob job;              // the job of the claimer's latest tile
     PairPlan plan[2];
     uint64_t bar[kPairStages];
-    uint32_t wsum[kLwWarps];
+    uint32_t wsum[3][kLwWarps];  // per batch of kLwThreads groups, each warp's ones of bit l + 1
 };
 
 template <typename Sym>
@@ -370,13 +375,14 @@ __device__ __forceinline__ void pair_tile(const PairLaunch &a, const PairStage &
         const uint32_t offz = (uint32_t)(gz & 31) * kW;
         const uint32_t B1 = ((offz + Zt * kW + 32 * kW - 1) / (32 * kW)) * (32 * kW) + (uint32_t)(go & 31) * kW;
         // Level bits of the lane's chunks, counts, and the split by bit l.
-        uint32_t x[kLwSteps][4], h[kLwSteps];
-        uint32_t cpk = 0;
+        constexpr int kPk = (kLwSteps + 1) / 2;  // two steps' counts per word (16 bits each)
+        uint32_t h[kLwSteps];
+        uint32_t cpk[kPk], lpk[kPk], tpk[kPk];
+#pragma unroll
+        for (int k2 = 0; k2 < kPk; k2++) cpk[k2] = 0;
 #pragma unroll
         for (int st = 0; st < kLwSteps; st++) {
             const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;
-            const uint4 vv = *reinterpret_cast<const uint4 *>(buf + q);
-            x[st][0] = vv.x, x[st][1] = vv.y, x[st][2] = vv.z, x[st][3] = vv.w;
             const uint32_t b0 = q / kW / 8;
             uint32_t hb = 0;
             if (kWhole || b0 < S.bits_bytes) {
@@ -385,12 +391,15 @@ __device__ __forceinline__ void pair_tile(const PairLaunch &a, const PairStage &
                 if (kSps == 4) hb = (sbits[b0] >> (4 * (lane & 1))) & 15u;
             }
             h[st] = hb;
-            cpk += (uint32_t)__popc(hb) << (16 * st);
+            cpk[st >> 1] += (uint32_t)__popc(hb) << (16 * (st & 1));
         }
-        uint32_t tpk;
-        const uint32_t lpk = warp_excl_scan(cpk, lane, tpk);
+        uint32_t wtot = 0;
+#pragma unroll
+        for (int k2 = 0; k2 < kPk; k2++) {
+            lpk[k2] = warp_excl_scan(cpk[k2], lane, tpk[k2]);
+            wtot += (tpk[k2] & 0xffffu) + (tpk[k2] >> 16);
+        }
         const uint64_t wx64 = S.pre[0][warp * kUpw] - P;  // ones of the tile before this warp's range
-        const uint32_t wtot = (tpk & 0xffffu) + (tpk >> 16);
         if (wx64 + wtot > t1 || wx64 > (uint64_t)warp * (kLwWarpBytes / kW)) {
             bad = true;  // this warp's prefix disagrees with the tile's count: it places nothing
         } else {
@@ -399,8 +408,11 @@ __device__ __forceinline__ void pair_tile(const PairLaunch &a, const PairStage &
 #pragma unroll
             for (int st = 0; st < kLwSteps; st++) {
                 const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;
-                const uint32_t o = wx + stx + ((lpk >> (16 * st)) & 0xffffu);
-                stx += (tpk >> (16 * st)) & 0xffffu;
+                const uint32_t sh16 = 16 * (st & 1);
+                const uint32_t o = wx + stx + ((lpk[st >> 1] >> sh16) & 0xffffu);
+                stx += (tpk[st >> 1] >> sh16) & 0xffffu;
+                const uint4 vv = *reinterpret_cast<const uint4 *>(buf + q);
+                const uint32_t x[4] = {vv.x, vv.y, vv.z, vv.w};
                 uint32_t po = B1 + o * kW;
                 const uint32_t C = offz + B1 + q;
 #pragma unroll
@@ -408,7 +420,7 @@ __device__ __forceinline__ void pair_tile(const PairLaunch &a, const PairStage &
                     if (kWhole || q / kW + kk < cnt) {
                         const bool one = (h[st] >> kk) & 1u;
                         const uint32_t at = one ? po : C + kk * kW - po;
-                        const uint32_t sv = sym_at<Sym>(x[st], kk);
+                        const uint32_t sv = sym_at<Sym>(x, kk);
                         if (kW == 1) A[at] = (unsigned char)sv;
                         if (kW == 2) *reinterpret_cast<uint16_t *>(A + at) = (uint16_t)sv;
                         if (kW == 4) *reinterpret_cast<uint32_t *>(A + at) = sv;
@@ -500,14 +512,15 @@ __device__ __forceinline__ void pair_tile(const PairLaunch &a, const PairStage &
 // The bits at shift bsh of a group of 32 symbols at g (32 w bytes, 16-byte
 // aligned in shared memory); x receives the group's 16-byte chunks.
 template <typename Sym>
-__device__ __forceinline__ uint32_t group_bits(const unsigned char *g, uint32_t bsh, uint4 (&x)[2 * sizeof(Sym)]) {
+__device__ __forceinline__ uint32_t group_bits(const unsigned char *g, uint32_t bsh, const BitGather &gg,
+                                               uint4 (&x)[2 * sizeof(Sym)]) {
     constexpr uint32_t kW = sizeof(Sym);
     uint32_t bits = 0;
 #pragma unroll
     for (uint32_t c = 0; c < 2 * kW; c++) {
         x[c] = *reinterpret_cast<const uint4 *>(g + 16 * c);
         const uint32_t w[4] = {x[c].x, x[c].y, x[c].z, x[c].w};
-        bits |= chunk_bits<Sym>(w, bsh) << (c * (16 / kW));
+        bits |= gather_bits<Sym>(w, gg, bsh) << (c * (16 / kW));
     }
     return bits;
 }
@@ -603,12 +616,14 @@ __global__ void __launch_bounds__(kLwThreads, 4) pair_pass_kernel(PairLaunch a) 
             break;
         }
         if (!runs) continue;  // the same in every thread
-        // Phase 2: A's 32-symbol groups (thread t: groups t and t + 256).
+        // Phase 2: A's 32-symbol groups (thread t: groups t, t + kLwThreads, ...).
         const uint32_t lv1 = L - 2 - a.l;  // level l + 1's bit
         const uint32_t G = plan.groups, ZG = plan.zgroups;
-        uint32_t gb[2] = {0, 0}, gm[2] = {0, 0}, gc[2] = {0, 0};
+        const BitGather g1 = bit_gather<Sym>(lv1);
+        uint32_t gb[kGB], gm[kGB], gc[kGB];
 #pragma unroll
-        for (int r = 0; r < 2; r++) {
+        for (int r = 0; r < kGB; r++) {
+            gb[r] = gm[r] = gc[r] = 0;
             const uint32_t gi = tid + r * kLwThreads;
             if (gi >= G) continue;
             const bool onesrun = gi >= ZG;
@@ -617,7 +632,7 @@ __global__ void __launch_bounds__(kLwThreads, 4) pair_pass_kernel(PairLaunch a) 
             const uint32_t len = onesrun ? plan.ot : plan.zt;
             const uint32_t abase = onesrun ? plan.b1 - (uint32_t)(dest & 31) * kW : 0u;
             uint4 x[2 * kW];
-            const uint32_t gbits = group_bits<Sym>(Ab + abase + kk * 32 * kW, lv1, x);
+            const uint32_t gbits = group_bits<Sym>(Ab + abase + kk * 32 * kW, lv1, g1, x);
             const uint32_t mask = run_word_mask(dest, len, kk);
             put_bits(plan.next1 + (dest >> 5) + kk, gbits, mask);
             gb[r] = gbits & mask;
@@ -625,32 +640,37 @@ __global__ void __launch_bounds__(kLwThreads, 4) pair_pass_kernel(PairLaunch a) 
             gc[r] = __popc(gbits & mask);
         }
         if (!plan.need_b) continue;  // level l + 1 is the last: no B
-        // Block scan of the groups' ones of bit l + 1, in group order.
-        uint32_t inc0 = gc[0];
+        // Block scan of the groups' ones of bit l + 1, in group order: batch
+        // r holds groups [r kLwThreads, (r + 1) kLwThreads).
+        uint32_t inc[kGB];
 #pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc0, dd);
-            if (lane >= dd) inc0 += y;
-        }
-        uint32_t inc1 = gc[1];
+        for (int r = 0; r < kGB; r++) {
+            inc[r] = gc[r];
 #pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc1, dd);
-            if (lane >= dd) inc1 += y;
+            for (int dd = 1; dd < 32; dd <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc[r], dd);
+                if (lane >= dd) inc[r] += y;
+            }
+            if (lane == 31) sh.wsum[r][warp] = inc[r];
         }
-        if (lane == 31) sh.wsum[warp] = inc0;
         __syncthreads();
-        uint32_t before = 0, total0 = 0;
+        uint32_t pref[kGB];
+        uint32_t done = 0;  // ones of the batches before r
 #pragma unroll
-        for (int w = 0; w < kLwWarps; w++) {
-            const uint32_t t = sh.wsum[w];
-            before += w < warp ? t : 0u;
-            total0 += t;
+        for (int r = 0; r < kGB; r++) {
+            uint32_t before = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kLwWarps; w++) {
+                const uint32_t t = sh.wsum[r][w];
+                before += w < warp ? t : 0u;
+                total += t;
+            }
+            pref[r] = done + before + inc[r] - gc[r];
+            done += total;
         }
-        const uint32_t pref[2] = {before + inc0 - gc[0], total0 + inc1 - gc[1]};
         // Phase 3: each group splits by bit l + 1 into B.
 #pragma unroll
-        for (int r = 0; r < 2; r++) {
+        for (int r = 0; r < kGB; r++) {
             const uint32_t gi = tid + r * kLwThreads;
             if (gi >= G) continue;
             const uint32_t onesrun = gi >= ZG ? 1u : 0u;
@@ -706,6 +726,8 @@ __global__ void __launch_bounds__(kLwThreads, 4) pair_pass_kernel(PairLaunch a) 
         }
         if (plan.next2 || plan.plane3) {
             const uint32_t lv2 = lv1 - 1;  // level l + 2's bit; bit l + 3 is lv2 - 1
+            const BitGather g2 = bit_gather<Sym>(lv2);
+            const BitGather g3 = bit_gather<Sym>(plan.plane3 ? lv2 - 1 : 0u);
             uint32_t nw[4], tot = 0;
 #pragma unroll
             for (int g = 0; g < 4; g++) {
@@ -720,7 +742,7 @@ __global__ void __launch_bounds__(kLwThreads, 4) pair_pass_kernel(PairLaunch a) 
                 const uint64_t dest = plan.d[g];
                 const unsigned char *gp = B + plan.boff[g] - (uint32_t)(dest & 31) * kW + kk * 32 * kW;
                 uint4 x[2 * kW];
-                const uint32_t b2 = group_bits<Sym>(gp, lv2, x);
+                const uint32_t b2 = group_bits<Sym>(gp, lv2, g2, x);
                 const uint32_t mask = run_word_mask(dest, plan.len[g], kk);
                 if (plan.next2) put_bits(plan.next2 + (dest >> 5) + kk, b2, mask);
                 if (plan.plane3) {
@@ -728,7 +750,7 @@ __global__ void __launch_bounds__(kLwThreads, 4) pair_pass_kernel(PairLaunch a) 
 #pragma unroll
                     for (uint32_t c = 0; c < 2 * kW; c++) {
                         const uint32_t w[4] = {x[c].x, x[c].y, x[c].z, x[c].w};
-                        b3 |= chunk_bits<Sym>(w, lv2 - 1) << (c * (16 / kW));
+                        b3 |= gather_bits<Sym>(w, g3, lv2 - 1) << (c * (16 / kW));
                     }
                     put_bits(plan.plane3 + (dest >> 5) + kk, b3, mask);
                 }
