@@ -27,8 +27,8 @@
 // pass writes it from the symbols.  The last level therefore needs no pass.
 //
 // GPU structure of the pass: a persistent CTA of 128 threads takes a
-// contiguous range of tiles and keeps four stages: the last warp claims a
-// tile three ahead and one thread issues TMA bulk copies (cp.async.bulk) of its
+// contiguous range of tiles and keeps two stages: the last warp claims a
+// tile one ahead and one thread issues TMA bulk copies (cp.async.bulk) of its
 // symbols, its unit prefixes and its slice of level l's bitmap into a
 // shared-memory stage while the CTA works on the current one.  Per tile:
 //   * a lane owns 16 consecutive bytes of each 512-byte warp step, so its
@@ -675,8 +675,8 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
 }
 
 constexpr size_t kLwSmem = kLwStages * (kLwTileBytes + kLwStageBits) + 2 * kLwSplitBytes + sizeof(LwShared);
-// Four CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA.
-static_assert(4 * (kLwSmem + 1024) <= 228 * 1024, "level pass shared memory");
+// Six CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA.
+static_assert(LwCfg<uint8_t>::kMinCtas * (kLwSmem + 1024) <= 228 * 1024, "level pass shared memory");
 
 template <typename Sym>
 static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass, bool counted, cudaStream_t st) {

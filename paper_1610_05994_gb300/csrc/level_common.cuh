@@ -20,7 +20,7 @@ constexpr uint32_t kLwTileBytes = kLwWarpBytes * kLwWarps;         // 8 KB
 // of the next bitmap, plus the reads of whole 32-symbol groups (4-byte
 // symbols: 2048 + 124 symbols at most).
 constexpr uint32_t kLwSplitBytes = kLwTileBytes + 512;
-constexpr int kLwStages = 4;
+constexpr int kLwStages = 2;                                       // input stages: the claimer stays one tile ahead
 constexpr uint32_t kLwStageBits = kLwTileBytes / 8;                 // a stage's copy of the level's bitmap (bytes)
 constexpr uint32_t kNoTile = 0xffffffffu;
 // The counts and prefixes are kept per unit of P_l: a warp's range or a rank
@@ -38,7 +38,7 @@ struct LwCfg {
     static constexpr int kSps = 16 / kW;                              // symbols per 16-byte chunk
     static constexpr uint32_t kTile = kLwTileBytes / kW;              // symbols per tile
     static constexpr uint32_t kBlocks = kTile / 512;                  // rank blocks per tile
-    static constexpr int kMinCtas = 4;                                // resident CTAs per SM
+    static constexpr int kMinCtas = 6;                                // resident CTAs per SM
     static constexpr uint32_t kUnits = lw_units(sizeof(Sym));         // count units per tile
     static constexpr uint32_t kUnitsPerWarp = kLwWarpBytes / lw_unit_bytes(sizeof(Sym));
     static constexpr uint32_t kPreCopy = kUnits + 2;                  // prefixes copied per tile
