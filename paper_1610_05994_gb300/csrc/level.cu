@@ -31,9 +31,9 @@
 // tile one ahead and one thread issues TMA bulk copies (cp.async.bulk) of its
 // symbols, its unit prefixes and its slice of level l's bitmap into a
 // shared-memory stage while the CTA works on the current one.  Per tile:
-//   * a lane owns 16 consecutive bytes of each 512-byte warp step, so its
-//     level bits are 16 (8, 4) consecutive bits of the bitmap copy; per-lane
-//     counts of two steps share one shuffle scan;
+//   * a lane owns 8 consecutive bytes of each 256-byte warp step, so its
+//     level bits are 8 (4, 2) consecutive bits of the bitmap copy; per-lane
+//     counts of three steps share one shuffle scan;
 //   * when the whole tile lies in one node (the common case: nodes are far
 //     larger than a tile except on the deepest levels of large alphabets),
 //     its zeros and ones go to two contiguous runs of P_{l+1}: each lane
@@ -396,7 +396,6 @@ template <typename Sym, bool kWhole>
 __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, const unsigned char *buf,
                                         const unsigned char *sbits, unsigned char *split, bool &bad, LwOut &out) {
     using Cfg = LwCfg<Sym>;
-    constexpr int kSps = Cfg::kSps;
     constexpr int kW = Cfg::kW;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t l = a.l;
@@ -411,26 +410,27 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     const uint32_t bsh = J.L - 1 - l;     // the level-l bit
     uint32_t *const next_words = J.next_words;
 
-    // Count: level bits of the lane's chunks (16, 8 or 4 consecutive bits of
-    // the level's bitmap, copied into the stage), per-lane and per-warp ones.
-    // The counts of two steps share a word (16 bits each) and one scan.
-    constexpr int kPk = (kLwSteps + 1) / 2;
-    uint32_t h[kLwSteps];
+    // Count: level bits of the lane's chunks, per-lane and per-warp ones.  A
+    // lane takes 8 consecutive bytes of each 256-byte warp step (8, 4 or 2
+    // symbols, i.e. that many consecutive bits of the level's bitmap copy):
+    // neighbouring lanes' run pointers are then about 4 bytes apart, one
+    // shared-memory bank, so the split's byte stores rarely conflict.  The
+    // counts of three steps share a word (10 bits each) and one scan.
+    constexpr int kSt = (int)(kLwWarpBytes / 256);  // warp steps of 8 bytes a lane
+    constexpr int kSpc = 8 / kW;                    // symbols of a lane's chunk
+    constexpr int kPk = (kSt + 2) / 3;
+    uint32_t h[kSt];
     uint32_t cpk[kPk], lpk[kPk], tpk[kPk];
 #pragma unroll
     for (int k2 = 0; k2 < kPk; k2++) cpk[k2] = 0;
 #pragma unroll
-    for (int st = 0; st < kLwSteps; st++) {
-        const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;  // the chunk's byte in the tile
-        const uint32_t b0 = q / kW / 8;  // the chunk's first bitmap byte in the tile
+    for (int st = 0; st < kSt; st++) {
+        const uint32_t q = warp * kLwWarpBytes + st * 256 + 8 * lane;  // the chunk's byte in the tile
+        const uint32_t bit = q / kW;                                   // its first symbol = bitmap bit
         uint32_t hb = 0;
-        if (kWhole || b0 < S.bits_bytes) {
-            if (kSps == 16) hb = *reinterpret_cast<const uint16_t *>(sbits + b0);
-            if (kSps == 8) hb = sbits[b0];
-            if (kSps == 4) hb = (sbits[b0] >> (4 * (lane & 1))) & 15u;
-        }
+        if (kWhole || bit / 8 < S.bits_bytes) hb = (sbits[bit / 8] >> (bit & 7)) & ((1u << kSpc) - 1u);
         h[st] = hb;
-        cpk[st >> 1] += (uint32_t)__popc(hb) << (16 * (st & 1));
+        cpk[st / 3] += (uint32_t)__popc(hb) << (10 * (st % 3));
     }
 #pragma unroll
     for (int k2 = 0; k2 < kPk; k2++) lpk[k2] = warp_excl_scan(cpk[k2], lane, tpk[k2]);
@@ -461,18 +461,18 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
             B1 = ((offz + Zt * kW + 32 * kW - 1) / (32 * kW)) * (32 * kW) + (uint32_t)(go & 31) * kW;
             uint32_t stx = 0;  // ones of earlier steps of this warp
 #pragma unroll
-            for (int st = 0; st < kLwSteps; st++) {
-                const uint32_t q = warp * kLwWarpBytes + st * 512 + 16 * lane;
-                const uint32_t sh16 = 16 * (st & 1);
-                const uint32_t o = wx + stx + ((lpk[st >> 1] >> sh16) & 0xffffu);  // ones before the chunk
-                stx += (tpk[st >> 1] >> sh16) & 0xffffu;
-                const uint4 v = *reinterpret_cast<const uint4 *>(buf + q);
-                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+            for (int st = 0; st < kSt; st++) {
+                const uint32_t q = warp * kLwWarpBytes + st * 256 + 8 * lane;
+                const uint32_t sh10 = 10 * (st % 3);
+                const uint32_t o = wx + stx + ((lpk[st / 3] >> sh10) & 0x3ffu);  // ones before the chunk
+                stx += (tpk[st / 3] >> sh10) & 0x3ffu;
+                const uint2 v = *reinterpret_cast<const uint2 *>(buf + q);
+                const uint32_t x[4] = {v.x, v.y, 0u, 0u};
                 // A one goes to po; a zero to C + k kW - po (its zeros-before, scaled).
                 uint32_t po = B1 + o * kW;
                 const uint32_t C = offz + B1 + q;
 #pragma unroll
-                for (int kk = 0; kk < kSps; kk++) {
+                for (int kk = 0; kk < kSpc; kk++) {
                     if (kWhole || q / kW + kk < cnt) {
                         const bool one = (h[st] >> kk) & 1u;
                         const uint32_t at = one ? po : C + kk * kW - po;
