@@ -182,19 +182,26 @@ wt_handle wt_build_chunked(const void *S, uint64_t n, uint64_t sigma, int sym_wi
                            void *stream);
 
 /*
- * access(i) for m device positions i[k] -> out[k] (device, uint32) by the
- * top-down walk of Section 2.2 simulated with rank on the level bitmaps.
- * i[k] >= n gives UINT32_MAX.
+ * access(i) for m device positions i[k] -> out[k] (device, uint32): the
+ * top-down walk of Section 2.2 (the worked example access(S, 24) = 't',
+ * Fig. 3), simulated on the pointerless levels with rank (Section 2.2, after
+ * Claude and Navarro 2008).  i[k] >= n gives UINT32_MAX.  Asynchronous on
+ * stream; the caller owns i and out.
  */
 wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, void *stream);
 
-/* rank_c(i) = occurrences of c[k] in [0, i[k]) -> out[k] (device arrays).
- * c >= sigma or i > n gives UINT64_MAX. */
+/* rank_c(i) = occurrences of c[k] in [0, i[k]) -> out[k] (device arrays),
+ * the operation rank_c(S, i) of Section 2.2 (read as half-open; the paper's
+ * inclusive rank on 0-based i is rank_c(i + 1)), by the same walk with the
+ * bits of c.  c >= sigma or i > n gives UINT64_MAX.  Asynchronous on stream. */
 wt_status wt_rank(wt_handle h, const uint32_t *c, const uint64_t *i, uint64_t m, uint64_t *out,
                   void *stream);
 
 /* select_c(j) = 0-based position of the j[k]-th occurrence of c[k] -> out[k]
- * (device arrays).  c >= sigma, j == 0 or j > count gives UINT64_MAX. */
+ * (device arrays), the operation select_c(S, j) of Section 2.2 (j is
+ * 1-based: the j-th appearance), by a descent to c's leaf and an ascent with
+ * select on each level's bitmap.  c >= sigma, j == 0 or j > count gives
+ * UINT64_MAX.  Asynchronous on stream. */
 wt_status wt_select(wt_handle h, const uint32_t *c, const uint64_t *j, uint64_t m, uint64_t *out,
                     void *stream);
 
@@ -202,16 +209,20 @@ wt_status wt_select(wt_handle h, const uint32_t *c, const uint64_t *j, uint64_t 
  * Mixed queries over several resident trees (the serving path): query k runs
  * op[k] (a wt_op) on trees[tree_idx[k]] with symbol c[k] and argument arg[k]
  * (i for access and rank, j for select); out[k] is the answer widened to
- * uint64 (access sentinel UINT32_MAX becomes UINT64_MAX).  trees is a host
- * array of ntrees handles; the other arrays are device arrays of length m.
+ * uint64 (access sentinel UINT32_MAX becomes UINT64_MAX).  The operations
+ * are those of Section 2.2 as for wt_access, wt_rank and wt_select; the
+ * paper batches no queries, this call is the serving pattern's.  trees is a
+ * host array of ntrees handles (ntrees bounds tree_idx: an index >= ntrees
+ * gives UINT64_MAX); the other arrays are device arrays of length m.
  */
 wt_status wt_query_multi(const wt_handle *trees, uint32_t ntrees, const uint32_t *tree_idx,
                          const uint8_t *op, const uint32_t *c, const uint64_t *arg, uint64_t m,
                          uint64_t *out, void *stream);
 
-/* Releases a handle.  The device memory is freed in stream order on the
- * stream the tree was built on, without a host wait; work on other streams
- * that still reads the tree must be complete (or ordered before) first. */
+/* Releases a handle (the tree of Section 2.2 and its directories).  The
+ * device memory is freed in stream order on the stream the tree was built
+ * on, without a host wait; work on other streams that still reads the tree
+ * must be complete (or ordered before) first.  NULL gives WT_ERR_ARG. */
 wt_status wt_free(wt_handle h);
 
 typedef struct {
@@ -224,7 +235,9 @@ typedef struct {
     uint64_t device_bytes; /* resident bytes of the tree */
 } wt_info_t;
 
-/* Shape of a built tree; waits for the build. */
+/* Shape of a built tree (n, sigma, L = ceil(lg sigma) levels of Section
+ * 2.2, the variant and layout that built it, its resident bytes); waits for
+ * the build.  Returns the build's status. */
 wt_status wt_info(wt_handle h, wt_info_t *out);
 
 typedef struct {
@@ -313,6 +326,19 @@ wt_status wt_level_step(const void *cur, uint64_t n, uint64_t sigma, int sym_wid
  */
 wt_status wt_node_starts_noalloc(const void *S, uint64_t n, uint64_t sigma, int sym_width, uint64_t *Hex,
                                  void *stream);
+
+/*
+ * Failure detection self test (no counterpart in the paper).  Every wait of
+ * the library's kernels is bounded: after its limit the kernel sets a
+ * give-up bit in an error word and returns, and the host turns that into
+ * WT_ERR_TIMEOUT with the CUDA context still usable.  This call runs that
+ * wait on an mbarrier in one thread for at most limit_ns (1 ns .. 1 s, else
+ * WT_ERR_ARG): with arrive == 0 nothing completes the barrier, so the wait
+ * runs out and the call returns WT_ERR_TIMEOUT; with arrive != 0 the thread
+ * arrives first and the call returns WT_OK.  err_word is one device uint32
+ * the caller owns (overwritten).  Synchronous on stream.
+ */
+wt_status wt_wait_selftest(uint64_t limit_ns, int arrive, uint32_t *err_word, void *stream);
 
 /*
  * Per-kernel timing (no counterpart in the paper; it times the hot path).

@@ -1479,7 +1479,7 @@ wt_status wt_query_multi(const wt_handle *trees, uint32_t ntrees, const uint32_t
     wt_status r = WT_OK;
     ProfScope p(K_Q_MULTI, 25.0 * m, st);
     if (cudaMemcpyAsync(d, ptrs.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        launch_query_multi(static_cast<const TreeDesc *const *>(d), tree_idx, op, c, arg, m, out, st) !=
+        launch_query_multi(static_cast<const TreeDesc *const *>(d), ntrees, tree_idx, op, c, arg, m, out, st) !=
             cudaSuccess) {
         cudaGetLastError();
         r = WT_ERR_CUDA;

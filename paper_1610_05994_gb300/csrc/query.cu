@@ -103,10 +103,15 @@ __global__ void __launch_bounds__(kQueryThreads) multi_kernel(const TreeDesc *co
                                                               const uint8_t *__restrict__ op,
                                                               const uint32_t *__restrict__ C,
                                                               const uint64_t *__restrict__ A, uint64_t m,
-                                                              uint64_t *__restrict__ out) {
+                                                              uint32_t ntrees, uint64_t *__restrict__ out) {
     const uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (q >= m) return;
-    const TreeDesc &t = *trees[tidx[q]];
+    const uint32_t ti = tidx[q];
+    if (ti >= ntrees) {  // a tree index outside the table: the sentinel, no read
+        out[q] = UINT64_MAX;
+        return;
+    }
+    const TreeDesc &t = *trees[ti];
     uint64_t r;
     switch (op[q]) {
         case WT_OP_ACCESS: {
@@ -146,11 +151,12 @@ cudaError_t launch_select(const TreeDesc *t, const uint32_t *c, const uint64_t *
     return cudaGetLastError();
 }
 
-cudaError_t launch_query_multi(const TreeDesc *const *trees, const uint32_t *tree_idx, const uint8_t *op,
+cudaError_t launch_query_multi(const TreeDesc *const *trees, uint32_t ntrees, const uint32_t *tree_idx,
+                               const uint8_t *op,
                                const uint32_t *c, const uint64_t *arg, uint64_t m, uint64_t *out,
                                cudaStream_t st) {
     if (m == 0) return cudaSuccess;
-    multi_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(trees, tree_idx, op, c, arg, m, out);
+    multi_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(trees, tree_idx, op, c, arg, m, ntrees, out);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -196,12 +196,12 @@ __device__ __forceinline__ uint64_t global_ns() {
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
 // Waits for the barrier phase with parity `phase`; false if it gave up
-// (after kWaitLimitNs).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+// (after limit_ns of %globaltimer).
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t phase, uint64_t limit_ns) {
     const uint32_t addr = smem_u32(bar);
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0;; i++) {
-        if ((i & 1023u) == 1023u && global_ns() - t0 > kWaitLimitNs) return false;
+        if ((i & 1023u) == 1023u && global_ns() - t0 > limit_ns) return false;
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -214,6 +214,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
     }
     return false;
 }
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) { return mbar_wait_for(bar, phase, kWaitLimitNs); }
 
 // ------------------------------------------------------ packed histogram
 // Alphabets too large for 32-bit shared bins: 16-bit bins, two per shared
@@ -532,7 +534,8 @@ cudaError_t launch_rank(const TreeDesc *t, const uint32_t *c, const uint64_t *i,
                         cudaStream_t st);
 cudaError_t launch_select(const TreeDesc *t, const uint32_t *c, const uint64_t *j, uint64_t m, uint64_t *out,
                           cudaStream_t st);
-cudaError_t launch_query_multi(const TreeDesc *const *trees, const uint32_t *tree_idx, const uint8_t *op,
+cudaError_t launch_query_multi(const TreeDesc *const *trees, uint32_t ntrees, const uint32_t *tree_idx,
+                               const uint8_t *op,
                                const uint32_t *c, const uint64_t *arg, uint64_t m, uint64_t *out,
                                cudaStream_t st);
 

@@ -78,6 +78,7 @@ _SIGNATURES = [
     ("wt_level_step", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_uint32, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("wt_node_starts_noalloc", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
+    ("wt_wait_selftest", C.c_int, [C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     ("wt_profile_begin", C.c_int, []),
     ("wt_profile_end", C.c_int, [C.POINTER(_KernelStat), C.c_uint32, C.POINTER(C.c_uint32)]),
 ]
@@ -385,6 +386,14 @@ def level_step(cur: torch.Tensor, sigma: int, l: int, hex_: torch.Tensor, want_n
                                 C.c_void_p(_dptr(hex_)), C.c_void_p(_dptr(words)), C.c_void_p(_dptr(R)),
                                 C.c_void_p(_dptr(nxt)), C.c_void_p(_stream(stream))), "wt_level_step")
     return words, R, nxt
+
+
+def wait_selftest(limit_ns: int, arrive: bool, stream=None) -> int:
+    """Runs the library's bounded device wait on a barrier (wt_wait_selftest)
+    and returns the status: ERR_TIMEOUT when nothing arrives, OK otherwise."""
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    return int(load().wt_wait_selftest(limit_ns, 1 if arrive else 0, C.c_void_p(_dptr(err)),
+                                       C.c_void_p(_stream(stream))))
 
 
 def profile_begin() -> None:

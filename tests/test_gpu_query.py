@@ -100,3 +100,20 @@ def test_query_multi_over_several_trees():
     got = W.query_multi(trees, torch.from_numpy(tidx).cuda(), torch.from_numpy(op).cuda(),
                         torch.from_numpy(c).cuda(), torch.from_numpy(arg).cuda()).cpu().numpy()
     assert np.array_equal(got, want)
+
+
+def test_query_multi_tree_index_outside_the_table_gives_the_sentinel():
+    """A tree index >= ntrees reads nothing and answers UINT64_MAX; the other
+    queries of the batch are unaffected."""
+    W = wt()
+    S = inputs.zipf(20_000, 96, 1.0, 7, np.uint8)
+    t = W.Tree.build(to_dev(S), 96)
+    tidx = to_dev(np.array([0, 1, 7, 0xFFFFFFFF, 0], np.uint32))
+    op = to_dev(np.array([0, 0, 1, 2, 1], np.uint8))
+    c = to_dev(np.array([0, 0, S[5], S[5], S[5]], np.uint32))
+    arg = to_dev(np.array([5, 5, 100, 1, 100], np.uint64))
+    got = W.query_multi([t], tidx, op, c, arg).cpu().numpy()
+    ones = np.uint64(2**64 - 1)
+    assert got[1] == ones and got[2] == ones and got[3] == ones
+    assert int(got[0]) == int(S[5])
+    assert int(got[4]) == int(np.sum(S[:100] == S[5]))
