@@ -274,7 +274,15 @@ struct Scratch {
     BuildScratch b{};
     uint32_t *plane[2] = {nullptr, nullptr};  // pair steps: bit l + 1 of P_l, packed like a bitmap
     uint64_t *ptab = nullptr;                 // pair tables
+    uint64_t *starts[2] = {nullptr, nullptr}; // node starts of levels l and l + 1 (rank_starts)
 };
+
+// Node tables by rank instead of a leaf histogram (launch_rank_tables) for
+// alphabets beyond the shared-memory histogram (more than 48K codes): there
+// the histogram needs global atomics (4.6 ms for 2^29 word ids over 2^20
+// codes, against about 0.02 ms per level for the rank tables).  Level 0's
+// count from the symbols then checks the symbol range.
+bool rank_starts(uint64_t sigma, uint32_t L) { return L > 0 && sigma > 48 * 1024; }
 
 // Which steps of a level-wise build take two levels in one pass: pair[l]
 // for a step covering levels l and l + 1.  A pair step needs 1- or 2-byte
@@ -307,12 +315,15 @@ double pair_step_bytes(uint64_t n, int w, bool store) {
 
 // pair_lmax: the deepest level whose pair step splits into P_{l+2} (needs a
 // pair table), or -1 when no step does; pairs: some step is a pair step.
+// by_rank: no leaf histogram (node tables by rank, rank_starts); the Hex
+// area then holds the two node-start arrays of consecutive levels.
 wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t sigma, uint32_t L, int width,
-                        bool need_levels, cudaStream_t st, bool pairs = false, int pair_lmax = -1) {
+                        bool need_levels, cudaStream_t st, bool pairs = false, int pair_lmax = -1,
+                        bool by_rank = false) {
     const uint64_t ntiles = ceil_div(n, lw_tile_elems(width));
-    const uint32_t R = hist_replicas(n, sigma);
-    const size_t hist = align256(R ? (size_t)R * sigma * 4 : sigma * 8);
-    const size_t hex = align256(((1ull << L) + 1) * 8);
+    const uint32_t R = by_rank ? 0u : hist_replicas(n, sigma);
+    const size_t hist = by_rank ? 256 : align256(R ? (size_t)R * sigma * 4 : sigma * 8);
+    const size_t hex = align256(((1ull << L) + 4) * 8);
     const size_t tab = need_levels ? align256((1ull << L) * 8) : 0;
     // A pair step keeps three count arrays (and their prefixes), way w at w * stride.
     const uint64_t units = lw_counts_bytes(n, width) / 4;
@@ -356,7 +367,9 @@ wt_status scratch_alloc(const Allocator &A, Scratch &sc, uint64_t n, uint64_t si
     sc.plane[1] = plane ? reinterpret_cast<uint32_t *>(p) : nullptr;
     p += plane;
     sc.ptab = ptab ? reinterpret_cast<uint64_t *>(p) : nullptr;
-    WT_CK(cudaMemsetAsync(sc.mem, 0, zeroed, st));
+    sc.starts[0] = sc.b.hex;
+    sc.starts[1] = sc.b.hex + (L ? (1ull << (L - 1)) + 2 : 2);
+    if (!by_rank) WT_CK(cudaMemsetAsync(sc.mem, 0, zeroed, st));
     return WT_OK;
 }
 
@@ -376,12 +389,14 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
                 table_levels |= 1u << l;
             }
         }
+    const bool by_rank = !any_pair && rank_starts(t->sigma, t->L);
     Scratch sc;
-    wt_status r = scratch_alloc(t->alloc, sc, t->n, t->sigma, t->L, t->width, true, st, any_pair, pair_lmax);
+    wt_status r =
+        scratch_alloc(t->alloc, sc, t->n, t->sigma, t->L, t->width, true, st, any_pair, pair_lmax, by_rank);
     if (r != WT_OK) return r;
     const BuildScratch &b = sc.b;
     const double nw = (double)t->n * t->width;
-    const uint32_t R = hist_replicas(t->n, t->sigma);
+    const uint32_t R = by_rank ? 0u : hist_replicas(t->n, t->sigma);
     const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
     const uint64_t units = lw_counts_bytes(t->n, t->width) / 4;
     LevelDesc *lv = t->h_desc.lv;
@@ -389,10 +404,12 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
     // (1-byte symbols): level 0's bitmap and unit counts, and the bitmaps
     // the first step ORs into zeroed.  For a pair step at level 0 also bit
     // L - 2 of S and the counts of groups 01 and 11.
-    const bool fuse0 = !R && t->L > 0 && level0_fusable(S, t->n, t->width, t->sigma);
+    const bool fuse0 = !by_rank && !R && t->L > 0 && level0_fusable(S, t->n, t->width, t->sigma);
     const bool pair0 = t->L > 0 && pair[0];
     const bool next0 = t->L > 1 && pass_writes_next_bits(level_boundaries(t->n, t->sigma, 0), ntiles, t->width);
-    {
+    if (by_rank) {
+        WT_CK(launch_root_starts(t->n, sc.starts[0], st));
+    } else {
         ProfScope p(K_HIST, nw, nw, st);
         if (R) {
             WT_CK(launch_histogram_replicated(S, t->n, t->width, t->sigma, reinterpret_cast<uint32_t *>(b.hist), R,
@@ -412,7 +429,7 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
             WT_CK(launch_histogram(S, t->n, t->width, t->sigma, b.hist, t->d_err, st));
         }
     }
-    if (t->L > 0) {
+    if (t->L > 0 && !by_rank) {
         const double leaves = (double)(1ull << t->L);
         {
             ProfScope p(K_NODE_STARTS, 8.0 * (t->sigma + leaves + 1), 8.0 * (t->sigma + leaves + 1), st);
@@ -427,6 +444,8 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
             WT_CK(launch_node_tables(b.hex, t->L, b.ob, b.ze, st, b.scan_tmp));
             WT_CK(launch_pair_tables(b.hex, t->L, table_levels, sc.ptab, st));
         }
+    }
+    if (t->L > 0) {
         const void *cur = S;
         void *bufs[2] = {b.ping, b.pong};
         int bi = 0, pi = 0;
@@ -478,10 +497,14 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
                 void *nxt = store ? bufs[bi] : nullptr;
                 const double vb = nw + t->n / 8.0 + t->n / 128.0 + (store ? nw : 0.0);
                 ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, has_next), vb, st);
+                // Without a histogram: level l's tables and C_{l+1} from rank at C_l.
+                const RankTables rt{lv[l], sc.starts[l & 1], b.ob + ((1ull << l) - 1), b.ze + ((1ull << l) - 1),
+                                    has_next ? sc.starts[(l + 1) & 1] : nullptr};
                 WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, lv[l],
                                         &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
                                         next_bits ? lv[l + 1].words : nullptr, t->d_err, b.job_slot, st,
-                                        l == 0 && fuse0));
+                                        l == 0 && fuse0, by_rank ? &rt : nullptr,
+                                        by_rank && l == 0 ? (uint32_t)t->sigma : 0u));
                 from_bits = next_bits;
                 plane_ok = false;
                 if (store) {

@@ -596,3 +596,54 @@ cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, ui
 }
 
 }  // namespace wt
+
+namespace wt {
+
+// ------------------------------------------------- node starts by rank
+// Node tables of level l without a leaf histogram.  Node v of level l spans
+// [C_l[v], C_l[v+1]); once level l's bitmap and rank directory exist, the
+// ones before each boundary give everything the pass needs:
+//   OB_l[v] = rank1_l(C_l[v])                      (ones before the node)
+//   ZE_l[v] = C_l[v+1] - rank1_l(C_l[v+1])          (zeros through its end)
+// and the children's starts on level l + 1 (Proposition 1: the zeros of
+// node v form node 2v, its ones node 2v + 1):
+//   C_{l+1}[2v] = C_l[v],  C_{l+1}[2v+1] = C_l[v+1] - rank1_l(C_l[v+1]) + rank1_l(C_l[v]).
+// One thread per node.  start_in: 2^l + 1 entries; start_out: 2^(l+1) + 1
+// (or nullptr on the last level).
+__global__ void __launch_bounds__(256) rank_tables_kernel(LevelDesc lv, uint64_t nodes,
+                                                          const uint64_t *__restrict__ start_in,
+                                                          uint64_t *__restrict__ ob, uint64_t *__restrict__ ze,
+                                                          uint64_t *__restrict__ start_out) {
+    const uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (v >= nodes) return;
+    const uint64_t c0 = start_in[v], c1 = start_in[v + 1];
+    const uint64_t r0 = rank1(lv, c0), r1 = rank1(lv, c1);
+    ob[v] = r0;
+    ze[v] = c1 - r1;
+    if (start_out) {
+        start_out[2 * v] = c0;
+        start_out[2 * v + 1] = c1 - r1 + r0;
+        if (v + 1 == nodes) start_out[2 * nodes] = c1;
+    }
+}
+
+__global__ void root_starts_kernel(uint64_t n, uint64_t *start) {
+    start[0] = 0;
+    start[1] = n;
+}
+
+cudaError_t launch_root_starts(uint64_t n, uint64_t *start, cudaStream_t st) {
+    root_starts_kernel<<<1, 1, 0, st>>>(n, start);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rank_tables(const LevelDesc &lv, uint32_t l, const uint64_t *start_in, uint64_t *ob,
+                               uint64_t *ze, uint64_t *start_out, cudaStream_t st) {
+    const uint64_t nodes = 1ull << l;
+    rank_tables_kernel<<<(unsigned)ceil_div(nodes, 256), 256, 0, st>>>(lv, nodes, start_in, ob, ze, start_out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace wt

@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kCountWarps;
     const uint32_t bsh_l = 1 + a.l;
+    bool bad = false;  // a symbol >= a.check_sigma (count from the symbols only)
     uint32_t k = 0;
     for (uint32_t g = blockIdx.x * kCountWarps + (threadIdx.x >> 5); g < a.total_tiles; g += nwarps) {
         if (k + 1 < a.njobs && a.tile_start[k + 1] <= g) {
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
                     for (int r = 0; r < 4; r++) {
                         const uint32_t x[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
                         const uint32_t hb = gather_bits<Sym>(x, gg, bsh);
+                        if (a.check_sigma) bad |= chunk_out_of_range<Sym>(x, a.check_sigma);
                         c[(h + r) / kPerUnit] += __popc(hb);
                         unsigned char *d = bl + (h + r) * (512 / sizeof(Sym) / 8);
                         if (sizeof(Sym) == 1) *reinterpret_cast<uint16_t *>(d) = (uint16_t)hb;
@@ -162,7 +164,9 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
                 for (int j = 0; j < (int)kU; j++)
                     for (uint32_t p0 = j * kUnitSyms; p0 < (j + 1) * kUnitSyms; p0 += 32) {
                         const uint32_t p = p0 + lane;
-                        const uint32_t bit = p < cnt ? ((uint32_t)S[base + p] >> bsh) & 1u : 0u;
+                        const uint32_t sv = p < cnt ? (uint32_t)S[base + p] : 0u;
+                        if (a.check_sigma && sv >= a.check_sigma) bad = true;
+                        const uint32_t bit = p < cnt ? (sv >> bsh) & 1u : 0u;
                         const uint32_t bal = __ballot_sync(0xffffffffu, bit);
                         c[j] += bit;
                         if (lane == 0 && w0 + p0 / 32 < nwords) words[w0 + p0 / 32] = bal;
@@ -187,6 +191,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
         }
         if (lane < (int)kU) J.cnt[(size_t)tile * kU + lane] = mine;
     }
+    if (bad) atomicOr(a.err, kErrSymbol);
 }
 
 // Unit prefixes of every job, pre[u] = ones of the job's units before u, in
@@ -679,7 +684,8 @@ constexpr size_t kLwSmem = kLwStages * (kLwTileBytes + kLwStageBits) + 2 * kLwSp
 static_assert(LwCfg<uint8_t>::kMinCtas * (kLwSmem + 1024) <= 228 * 1024, "level pass shared memory");
 
 template <typename Sym>
-static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass, bool counted, cudaStream_t st) {
+static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass, bool counted, cudaStream_t st,
+                             const RankTables *rt) {
     // Persistent grid: every resident CTA slot, at most one CTA per tile.
     static int slots = 0, sms = 0;
     if (!slots) {
@@ -712,6 +718,10 @@ static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass,
     scan_sums_kernel<<<sg, 1024, 0, st>>>(a);
     scan_segs_kernel<<<sg, 1024, 0, st>>>(a);
     note_launches(2);
+    if (rt) {  // the level's node tables from its directory (no histogram)
+        const cudaError_t e = launch_rank_tables(rt->lv, a.l, rt->start_in, rt->ob, rt->ze, rt->start_out, st);
+        if (e != cudaSuccess) return e;
+    }
     if (do_pass) {
         const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
         level_pass_kernel<Sym><<<grid, kLwThreads, kLwSmem, st>>>(a);
@@ -743,7 +753,8 @@ LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint3
 
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
                               uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
-                              uint32_t *err, cudaStream_t st, bool counted) {
+                              uint32_t *err, cudaStream_t st, bool counted, const RankTables *rt,
+                              uint32_t check_sigma) {
     if (njobs == 0 || total_tiles == 0) return cudaSuccess;
     LevelLaunch a;
     a.jobs = jobs;
@@ -756,10 +767,11 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.segs = (uint32_t)ceil_div((uint64_t)(max_job_tiles ? max_job_tiles : 1) * a.units, kScanSeg);
     a.err = err;
     a.ways = 1;
+    a.check_sigma = check_sigma;
     switch (width) {
-        case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, counted, st);
-        case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, counted, st);
-        case 4: return launch_lw<uint32_t>(a, from_bits, do_pass, counted, st);
+        case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, counted, st, rt);
+        case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, counted, st, rt);
+        case 4: return launch_lw<uint32_t>(a, from_bits, do_pass, counted, st, rt);
     }
     return cudaErrorInvalidValue;
 }
@@ -810,7 +822,7 @@ cudaError_t launch_level_directory(uint64_t n, int width, uint32_t L, uint32_t l
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
                               uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
-                              cudaStream_t st, bool counted) {
+                              cudaStream_t st, bool counted, const RankTables *rt, uint32_t check_sigma) {
     if (n == 0) return cudaSuccess;
     const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, cnt, pre, next_words);
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
@@ -819,7 +831,8 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, from_bits, l + 1 < L, err, st, counted);
+    return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, from_bits, l + 1 < L, err, st, counted, rt,
+                             check_sigma);
 }
 
 }  // namespace wt

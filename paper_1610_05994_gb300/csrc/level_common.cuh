@@ -55,7 +55,38 @@ struct LevelLaunch {
     uint32_t units, upb;         // count units per tile and per rank block
     uint32_t *err;
     uint32_t ways;               // count arrays the scan turns into prefixes (1, or 3 for a pair step)
+    uint32_t check_sigma;        // > 0: the count pass from the symbols flags any symbol >= check_sigma
 };
+
+// Whether some symbol of a 16-byte chunk is >= sigma (sigma >= 1).  For bytes
+// with sigma <= 128: b >= 128 is out of range, and for b < 128 the byte
+// (b | 0x80) - sigma keeps its top bit exactly when b >= sigma, with no
+// borrow between bytes; for 128 < sigma < 256 the same test on the low
+// seven bits against sigma - 128, for bytes with the top bit set.
+template <typename Sym>
+__device__ __forceinline__ bool chunk_out_of_range(const uint32_t (&x)[4], uint32_t sigma) {
+    if (sizeof(Sym) == 1) {
+        if (sigma >= 256) return false;
+        uint32_t t = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (sigma <= 128) {
+                t |= (x[q] & 0x80808080u) | (((x[q] | 0x80808080u) - sigma * 0x01010101u) & 0x80808080u);
+            } else {
+                const uint32_t y = (x[q] & 0x7f7f7f7fu) | 0x80808080u;
+                t |= x[q] & (y - (sigma - 128u) * 0x01010101u) & 0x80808080u;
+            }
+        }
+        return t != 0;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 16 / (int)sizeof(Sym); k++) {
+        const uint32_t v = sizeof(Sym) == 2 ? (x[k >> 1] >> (16 * (k & 1))) & 0xffffu : x[k];
+        bad |= v >= sigma;
+    }
+    return bad;
+}
 
 // Job of global tile t: the largest k with tile_start[k] <= t.
 __device__ __forceinline__ uint32_t find_job(const LevelLaunch &a, uint32_t t) {

@@ -340,6 +340,12 @@ cudaError_t launch_node_starts(const uint64_t *hist, uint64_t sigma, uint32_t L,
 cudaError_t launch_node_tables(const uint64_t *hex, uint32_t L, uint64_t *ob, uint64_t *ze,
                                cudaStream_t st, uint64_t *tmp = nullptr);
 size_t scan_tmp_bytes(uint32_t L);
+// Node tables without a histogram (large alphabets): C_0 = {0, n}; after
+// level l's count and scan, level l's tables and C_{l+1} from rank1 of
+// level l at the node boundaries C_l (start_out nullptr on the last level).
+cudaError_t launch_root_starts(uint64_t n, uint64_t *start, cudaStream_t st);
+cudaError_t launch_rank_tables(const LevelDesc &lv, uint32_t l, const uint64_t *start_in, uint64_t *ob,
+                               uint64_t *ze, uint64_t *start_out, cudaStream_t st);
 
 // Kernels (b)+(c): the level passes (level.cu).  Each level: a count pass
 // stores the level-l ones of every tile of P_l, a scan turns them into each
@@ -445,14 +451,24 @@ cudaError_t launch_pair_step(const PairJob &j, int width, uint32_t l, LevelDesc 
 // max_job_tiles: the most tiles of any one job.
 // counted: the units' counts (and level l's bitmap) are already in place
 // (level 0 folded into the histogram): no count pass.
+// rt: compute the level's node tables (and the next level's node starts)
+// from its directory between the scan and the pass (launch_rank_tables).
+// check_sigma > 0: the count from the symbols flags any symbol >= it.
+struct RankTables {
+    LevelDesc lv;
+    const uint64_t *start_in;
+    uint64_t *ob, *ze, *start_out;
+};
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
                               uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
-                              uint32_t *err, cudaStream_t st, bool counted = false);
+                              uint32_t *err, cudaStream_t st, bool counted = false, const RankTables *rt = nullptr,
+                              uint32_t check_sigma = 0);
 // One sequence (job_slot: level_job_slot_bytes() of device memory).
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
                               uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
-                              cudaStream_t st, bool counted = false);
+                              cudaStream_t st, bool counted = false, const RankTables *rt = nullptr,
+                              uint32_t check_sigma = 0);
 
 // The prefix scan alone of level l (ways count arrays, way 0 with the
 // directory), over jobs already in device memory.
