@@ -692,6 +692,20 @@ def roofline_of(stats: dict, steps: int):
                     "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(name),
                     "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
                     "avg_launch_ms": st["total_ms"] / st["launches"]}
+        if st.get("variant_bytes"):
+            vb = st["variant_bytes"] / (st["total_ms"] * 1e-3) / 1e9
+            roofline["variant_bytes_achieved"] = vb
+            roofline["variant_bytes_frac"] = vb / peak
+        # The whole build against the level-wise model's total bytes (the
+        # histogram term n w is the read of S for the counts: the histogram,
+        # or level 0's count pass when the node tables come by rank).
+        build = [k for k in ("histogram", "level0_count", "node_starts", "node_tables", "level_pass") if k in stats]
+        if "level_pass" in build:
+            b_bytes = sum(stats[k]["alg_bytes"] for k in build if k in ("histogram", "level0_count", "level_pass"))
+            b_ms = sum(stats[k]["total_ms"] for k in build)
+            ach = b_bytes / (b_ms * 1e-3) / 1e9
+            roofline["build"] = {"kernels": build, "achieved": ach, "frac": ach / peak,
+                                 "ms_per_step": b_ms / steps}
     kernels = {k: {"launches": v["launches"], "cuda_kernels": v["kernels"], "ms_per_step": v["total_ms"] / steps,
                    "GBps": v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9 if v["total_ms"] > 0 else None}
                for k, v in stats.items()}

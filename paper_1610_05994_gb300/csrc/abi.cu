@@ -79,11 +79,11 @@ double level_step_bytes(uint64_t n, int w, bool has_next) {
 // kernel.
 enum KernelId {
     K_HIST = 0, K_NODE_STARTS, K_NODE_TABLES, K_LEVEL_PASS, K_DD_COUNT, K_DD_SCAN, K_DD_WRITE,
-    K_Q_ACCESS, K_Q_RANK, K_Q_SELECT, K_Q_MULTI, K_MERGE_STARTS, K_MERGE, K_COUNT
+    K_Q_ACCESS, K_Q_RANK, K_Q_SELECT, K_Q_MULTI, K_MERGE_STARTS, K_MERGE, K_LEVEL0_COUNT, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {"histogram",  "node_starts", "node_tables",  "level_pass",   "dd_count",
                                      "dd_scan",    "dd_write",    "query_access", "query_rank",   "query_select",
-                                     "query_multi", "merge_starts", "merge"};
+                                     "query_multi", "merge_starts", "merge",      "level0_count"};
 
 struct ProfRecord {
     int kid;
@@ -277,12 +277,15 @@ struct Scratch {
     uint64_t *starts[2] = {nullptr, nullptr}; // node starts of levels l and l + 1 (rank_starts)
 };
 
-// Node tables by rank instead of a leaf histogram (launch_rank_tables) for
-// alphabets beyond the shared-memory histogram (more than 48K codes): there
-// the histogram needs global atomics (4.6 ms for 2^29 word ids over 2^20
-// codes, against about 0.02 ms per level for the rank tables).  Level 0's
-// count from the symbols then checks the symbol range.
-bool rank_starts(uint64_t sigma, uint32_t L) { return L > 0 && sigma > 48 * 1024; }
+// Node tables by rank instead of a leaf histogram (launch_rank_tables): the
+// level passes need only rank1 of each level at its node boundaries, which
+// its own directory gives after its scan.  Level 0's count from the symbols
+// then checks the symbol range.  For alphabets beyond the shared-memory
+// histogram (more than 48K codes) the histogram needs global atomics (4.6 ms
+// for 2^29 word ids over 2^20 codes, against about 0.02 ms per level for the
+// rank tables); for small alphabets the histogram's shared atomics cost more
+// than level 0's plain count pass.
+bool rank_starts(uint64_t sigma, uint32_t L) { return L > 0 && sigma >= 2; }
 
 // Which steps of a level-wise build take two levels in one pass: pair[l]
 // for a step covering levels l and l + 1.  A pair step needs 1- or 2-byte
@@ -408,7 +411,14 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
     const bool pair0 = t->L > 0 && pair[0];
     const bool next0 = t->L > 1 && pass_writes_next_bits(level_boundaries(t->n, t->sigma, 0), ntiles, t->width);
     if (by_rank) {
+        // Level 0's count pass from S (level 0's bitmap, unit counts, the
+        // symbol range): the level-wise model's read of S for the counts,
+        // profiled on its own as the histogram was.
+        ProfScope p(K_LEVEL0_COUNT, nw, nw + t->n / 8.0, st);
         WT_CK(launch_root_starts(t->n, sc.starts[0], st));
+        const bool nb0 = t->L > 1 && pass_writes_next_bits(level_boundaries(t->n, t->sigma, 0), ntiles, t->width);
+        WT_CK(launch_level_count(S, t->n, t->width, t->L, 0, lv[0], b.cnt, nb0 ? lv[1].words : nullptr, t->d_err,
+                                 b.job_slot, st, (uint32_t)t->sigma));
     } else {
         ProfScope p(K_HIST, nw, nw, st);
         if (R) {
@@ -503,8 +513,7 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
                 WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, lv[l],
                                         &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
                                         next_bits ? lv[l + 1].words : nullptr, t->d_err, b.job_slot, st,
-                                        l == 0 && fuse0, by_rank ? &rt : nullptr,
-                                        by_rank && l == 0 ? (uint32_t)t->sigma : 0u));
+                                        l == 0 && (fuse0 || by_rank), by_rank ? &rt : nullptr));
                 from_bits = next_bits;
                 plane_ok = false;
                 if (store) {

@@ -805,6 +805,43 @@ size_t level_job_bytes() { return sizeof(LevelJob); }
 
 size_t level_job_slot_bytes() { return (sizeof(LevelJob) + 2 * sizeof(uint32_t) + 255) & ~size_t(255); }
 
+cudaError_t launch_level_count(const void *cur, uint64_t n, int width, uint32_t L, uint32_t l, LevelDesc lv,
+                               uint32_t *cnt, uint32_t *next_words, uint32_t *err, void *job_slot, cudaStream_t st,
+                               uint32_t check_sigma) {
+    if (n == 0) return cudaSuccess;
+    LevelJob j = make_level_job(cur, nullptr, n, width, L, l, nullptr, nullptr, lv, nullptr, cnt, nullptr,
+                                next_words);
+    LevelJob *dj = static_cast<LevelJob *>(job_slot);
+    uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
+    put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
+    note_launches(1);
+    LevelLaunch a{};
+    a.jobs = dj;
+    a.tile_start = ts;
+    a.njobs = 1;
+    a.total_tiles = j.ntiles;
+    a.l = l;
+    a.units = lw_units((uint32_t)width);
+    a.upb = 512u * (uint32_t)width / lw_unit_bytes((uint32_t)width);
+    a.segs = 1;
+    a.err = err;
+    a.ways = 1;
+    a.check_sigma = check_sigma;
+    const uint32_t cw = (j.ntiles + kCountWarps - 1) / kCountWarps;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t g0 = cw < (uint32_t)(sms * 8) ? cw : (uint32_t)(sms * 8);
+    switch (width) {
+        case 1: count_kernel<uint8_t, false><<<g0, kCountThreads, 0, st>>>(a); break;
+        case 2: count_kernel<uint16_t, false><<<g0, kCountThreads, 0, st>>>(a); break;
+        case 4: count_kernel<uint32_t, false><<<g0, kCountThreads, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_level_directory(uint64_t n, int width, uint32_t L, uint32_t l, LevelDesc lv, uint64_t *ones_out,
                                    uint32_t *cnt, uint64_t *pre, uint32_t *err, void *job_slot, cudaStream_t st) {
     if (n == 0) return cudaSuccess;

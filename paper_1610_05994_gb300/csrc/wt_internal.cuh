@@ -474,6 +474,13 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
 // directory), over jobs already in device memory.
 cudaError_t launch_level_scans(int width, uint32_t l, const LevelJob *jobs, uint32_t njobs, uint32_t max_job_tiles,
                                uint32_t ways, cudaStream_t st);
+// The count pass of level l alone, from the symbols cur (writes level l's
+// bitmap and unit counts, zeroes next_words when not nullptr, flags symbols
+// >= check_sigma when it is > 0); launch_level_pass with counted = true
+// then runs the scan and the pass.
+cudaError_t launch_level_count(const void *cur, uint64_t n, int width, uint32_t L, uint32_t l, LevelDesc lv,
+                               uint32_t *cnt, uint32_t *next_words, uint32_t *err, void *job_slot, cudaStream_t st,
+                               uint32_t check_sigma);
 // Level l's directory from its bitmap (already written): count from the
 // bitmap and the prefix scan, no pass.
 cudaError_t launch_level_directory(uint64_t n, int width, uint32_t L, uint32_t l, LevelDesc lv, uint64_t *ones_out,
