@@ -579,6 +579,66 @@ def run_merge(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+TUNE_CLASSES = [(4, 1, "uniform"), (20, 1, "zipf"), (96, 1, "zipf"), (256, 1, "uniform"), (1000, 2, "zipf"),
+                 (65536, 2, "zipf"), (1 << 20, 4, "zipf")]
+TUNE_LOG2N = (12, 14, 16, 18, 20, 22, 24, 26, 28)
+
+
+def run_tune(args, ws, rank, local):
+    """The autotuner's measurement: build time of every variant (one level
+    per pass, two levels per pass, dd-direct where it applies) for each
+    (alphabet, width) class and n = 2^12 .. 2^28, as the median device time
+    between CUDA events around wt_build_async calls on the default stream
+    (a small build is bound by its launches, so the host's launch cost is in
+    the figure).  Prints one JSON line with the table and the fastest
+    variant per entry."""
+    import torch
+
+    from paper_1610_05994_gb300 import build as B
+    from paper_1610_05994_gb300 import wt as W
+
+    torch.cuda.set_device(local)
+    B.build_library()
+    W.load()
+    dev = torch.device("cuda", local)
+    reps = max(3, args.steps)
+    table = {}
+    for sigma, width, dist in TUNE_CLASSES:
+        dt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[width]
+        big = (inputs.zipf(1 << max(TUNE_LOG2N), sigma, 1.0, 77, dt) if dist == "zipf"
+               else inputs.uniform(1 << max(TUNE_LOG2N), sigma, 77, dt))
+        big_d = torch.from_numpy(big).to(dev)
+        row = {}
+        for lg in TUNE_LOG2N:
+            S = big_d[: 1 << lg]
+            cells = {}
+            variants = [W.VARIANT_LEVELWISE, W.VARIANT_PAIRS] + ([W.VARIANT_DD] if width == 1 else [])
+            for var in variants:
+                for _ in range(2):
+                    W.Tree.build(S, sigma, variant=var).free()
+                times = []
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record()
+                    t = W.Tree.build(S, sigma, variant=var, wait=False)
+                    e1.record()
+                    t.wait()
+                    times.append(e0.elapsed_time(e1))
+                    t.free()
+                cells[{1: "levelwise", 2: "dd", 3: "pairs"}[var]] = statistics.median(times)
+            best = min(cells, key=cells.get)
+            row[lg] = {"ms": cells, "best": best}
+        table[f"sigma={sigma} w={width} {dist}"] = row
+        del big_d
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return
+    print(json.dumps({"metric": "build time per variant (ms, median)", "unit": "ms", "n_gpus": ws,
+                      "reps": reps, "table": table}), flush=True)
+
+
 def run_matrix(args, ws, rank, local):
     """Wavelet matrices of the default sequences (text and DNA, 2^30 symbols
     each): a step builds both, device-resident; the same builds from pinned
@@ -1017,7 +1077,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    runners = {"batch": run_batch, "serve": run_serve, "locality": run_locality, "merge": run_merge,
+    runners = {"batch": run_batch, "serve": run_serve, "locality": run_locality, "merge": run_merge, "tune": run_tune,
                "matrix": run_matrix}
     ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + sorted(runners), default="text+dna")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured build requests")

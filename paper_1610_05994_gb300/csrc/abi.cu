@@ -640,24 +640,37 @@ wt_status enqueue_dd(wt_tree *t, const void *S, cudaStream_t st) {
     return r;
 }
 
-// Variant choice (AUTO), from measurements on GB300:
-//  * dd-direct where it applies (one byte per symbol, sigma <= 256,
-//    n < 2^32) and g_dd_faster says it beat the level-wise build for that
-//    number of levels;
-//  * two levels per pass where g_pairs_faster says so for the symbol width;
-//  * otherwise one level per pass.
-// The level step is bound by the ALU pipe (integer issue), not by HBM: a
-// pair step spends two byte splits per symbol plus three bit extractions,
-// about what two one-level steps spend, so it has not been faster
-// (2^28-symbol text: 25.7 ALU thread-instructions per symbol for a pair
-// step against 2 x 10.3 for two one-level steps).
-constexpr bool g_dd_faster[9] = {false, false, false, false, false, false, false, false, false};  // by L
-constexpr bool g_pairs_faster[3] = {false, false, false};                                      // by width 1, 2, 4
+// Variant choice (AUTO): the fastest variant measured on GB300 for the
+// entry's (symbol width, levels L, n), from `bench.py --workload tune`
+// (median build time of each variant over n = 2^12 .. 2^28 for sigma in
+// {4, 20, 96, 256} bytes, {1000, 65536} 2-byte and 2^20 4-byte codes).
+//  * Small builds are bound by their launches (one level per pass takes four
+//    or five launches per level), so dd-direct, three launches in all, wins
+//    for 1-byte codes up to kDdMaxLog2N[L] (for example sigma = 96:
+//    0.25 ms against 0.39 ms at 2^22), and two levels per pass, half the
+//    level steps, wins for 2-byte codes with up to kPairsMaxL levels up to
+//    2^kPairsMaxLog2N (sigma = 1000: 0.49 against 0.52 ms at 2^22).
+//  * Large builds are bound by the level pass's ALU work, where one level per
+//    pass is fastest (sigma = 96 at 2^28: 2.07 ms against 2.60 ms for two
+//    levels per pass and 3.95 ms for dd-direct; sigma = 65536: one level per
+//    pass at every n).
+// n between measured sizes takes the rule of the next measured size above.
+constexpr uint8_t kDdMaxLog2N[9] = {0, 20, 20, 24, 24, 24, 24, 24, 24};  // by L, 1-byte codes
+constexpr uint32_t kPairsMaxL = 12;
+constexpr uint32_t kPairsMaxLog2N = 22;
+
+uint32_t ceil_log2(uint64_t n) {
+    uint32_t k = 0;
+    while (k < 63 && (1ull << k) < n) k++;
+    return k;
+}
 
 int choose_variant(uint64_t n, uint64_t sigma, int width) {
     const uint32_t L = levels_of(sigma);
-    if (dd_supported(n, sigma, width) && L <= 8 && g_dd_faster[L]) return WT_VARIANT_DD;
-    if (g_pairs_faster[width == 1 ? 0 : (width == 2 ? 1 : 2)]) {
+    const uint32_t lg = ceil_log2(n);
+    if (width == 1 && L >= 1 && L <= 8 && dd_supported(n, sigma, width) && lg <= kDdMaxLog2N[L])
+        return WT_VARIANT_DD;
+    if (width == 2 && L >= 2 && L <= kPairsMaxL && lg <= kPairsMaxLog2N) {
         const std::vector<uint8_t> pair = level_schedule(n, sigma, L, width, true);
         for (uint8_t p : pair)
             if (p) return WT_VARIANT_PAIRS;

@@ -236,3 +236,19 @@ def test_large_alphabet_flags_out_of_range_symbols():
     with pytest.raises(W.WTError) as e:
         W.Tree.build(to_dev(S), sigma)
     assert e.value.status == W.ERR_SYMBOL_RANGE
+
+
+@pytest.mark.parametrize("sigma,dtype,log2n,want", [
+    (96, np.uint8, 20, "dd"), (4, np.uint8, 20, "dd"), (4, np.uint8, 22, "levelwise"),
+    (96, np.uint8, 25, "levelwise"), (1000, np.uint16, 20, "pairs"), (1000, np.uint16, 23, "levelwise"),
+    (65536, np.uint16, 18, "levelwise"), (1 << 20, np.uint32, 18, "levelwise")])
+def test_auto_follows_the_measured_table_and_is_bit_exact(sigma, dtype, log2n, want):
+    """The autotuner's choice (the measured table of choose_variant) for a few
+    (width, levels, n) entries, and the tree it builds equals the oracle's."""
+    W = wt()
+    n = (1 << log2n) - 3
+    S = inputs.zipf(n, sigma, 1.0, 600 + log2n, dtype)
+    t = W.Tree.build(to_dev(S), sigma)
+    names = {W.VARIANT_LEVELWISE: "levelwise", W.VARIANT_DD: "dd", W.VARIANT_PAIRS: "pairs"}
+    assert names[t.info()["variant"]] == want
+    compare_tree(t, S, sigma)
