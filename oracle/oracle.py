@@ -270,3 +270,76 @@ def level_bit(S: np.ndarray, sigma: int, l: int, p: int) -> int:
     """B_l[p] for a single position, from the definition."""
     L = levels(sigma)
     return (level_symbol(S, sigma, l, p) >> (L - 1 - l)) & 1
+
+
+# ------------------------------------------------------ alphabet remapping
+# Section 3 (first paragraph): the construction assumes the codes of Sigma
+# are contiguous; when they are not, "a bitmap is used to remap the sequence
+# to a contiguous alphabet" (after Claude and Navarro 2008).  Written from that
+# definition: over the code universe [0, U), bit c of the alphabet bitmap is
+# set exactly when c occurs in S; sigma' = its number of ones; a code c maps
+# to rank1(bitmap, c), the number of alphabet codes below c, so S' takes
+# values in [0, sigma').  The tree is the tree of S' over sigma'.  Queries
+# map through the bitmap: access gives back the c with rank1(bitmap, c) = the
+# tree's answer (select1 of the bitmap); rank and select of a code c < U that
+# does not occur give 0 (for 0 <= i <= n) and the sentinel; a code c >= U
+# gives the sentinel.  The alphabet bitmap uses the level layout (bit c at
+# byte c >> 3, bit c & 7, padded with zeros to whole 512-bit blocks), so its
+# directory is the level directory of `directory`.
+
+def remap_alphabet(S: np.ndarray, universe: int):
+    """(alphabet bitmap bytes, codes of the alphabet in increasing order,
+    S' = the remapped sequence as uint32, sigma' = the alphabet's size, at
+    least 1 so that an empty S still has a tree, of no levels)."""
+    S = np.ascontiguousarray(S)
+    if len(S) and int(S.max()) >= universe:
+        raise OracleError("symbol out of range")
+    present = np.zeros(universe, dtype=bool)
+    present[S.astype(np.int64)] = True
+    codes = np.flatnonzero(present).astype(np.uint64)
+    mapped = np.searchsorted(codes, S.astype(np.uint64)).astype(np.uint32)
+    bits = np.zeros(level_bytes(universe) * 8, dtype=np.uint8)
+    bits[:universe] = present
+    return np.packbits(bits, bitorder="little"), codes, mapped, max(1, len(codes))
+
+
+def remap_access(codes: np.ndarray, bits: np.ndarray, n: int, sigma_r: int, i) -> np.ndarray:
+    """access(i) on the remapped tree, mapped back to the original codes
+    (UINT32_MAX for i >= n)."""
+    r = access(bits, n, sigma_r, i).astype(np.uint64)
+    out = np.full(len(r), 0xFFFFFFFF, dtype=np.uint64)
+    ok = r != 0xFFFFFFFF
+    out[ok] = codes[r[ok].astype(np.int64)]
+    return out.astype(np.uint32)
+
+
+def _remap_codes(codes: np.ndarray, universe: int, c):
+    c = np.asarray(c, dtype=np.uint64)
+    pos = np.searchsorted(codes, c)
+    present = (pos < len(codes)) & (codes[np.minimum(pos, max(len(codes) - 1, 0))] == c) if len(codes) else \
+        np.zeros(len(c), dtype=bool)
+    return pos.astype(np.uint32), present, c < np.uint64(universe)
+
+
+def remap_rank(codes: np.ndarray, universe: int, bits: np.ndarray, n: int, sigma_r: int, c, i) -> np.ndarray:
+    """rank_c(i) over [0, i) on the remapped tree for original codes c."""
+    i = np.asarray(i, dtype=np.uint64)
+    cr, present, inside = _remap_codes(codes, universe, c)
+    out = np.full(len(i), 2**64 - 1, dtype=np.uint64)
+    sel = present & inside
+    if sel.any():
+        out[sel] = rank(bits, n, sigma_r, cr[sel], i[sel])
+    absent = inside & ~present & (i <= np.uint64(n))
+    out[absent] = 0
+    return out
+
+
+def remap_select(codes: np.ndarray, universe: int, bits: np.ndarray, n: int, sigma_r: int, c, j) -> np.ndarray:
+    """select_c(j) (j 1-based) on the remapped tree for original codes c."""
+    j = np.asarray(j, dtype=np.uint64)
+    cr, present, inside = _remap_codes(codes, universe, c)
+    out = np.full(len(j), 2**64 - 1, dtype=np.uint64)
+    sel = present & inside
+    if sel.any():
+        out[sel] = select(bits, n, sigma_r, cr[sel], j[sel])
+    return out

@@ -484,3 +484,59 @@ def test_matrix_sigma_one_has_no_levels():
     assert O.wm_access(bits, 10, 1, [0, 9, 10]).tolist() == [0, 0, 0xFFFFFFFF]
     assert O.wm_rank(bits, 10, 1, [0, 0], [4, 10]).tolist() == [4, 10]
     assert O.wm_select(bits, 10, 1, [0, 0], [1, 11]).tolist() == [0, 2**64 - 1]
+
+
+# ------------------------------------------------------- alphabet remapping
+
+@pytest.mark.parametrize("universe,alphabet,dtype", [
+    (1 << 20, [0, 7, 1000, (1 << 20) - 1], np.uint32),
+    (65536, [3, 4, 5, 60000, 65535], np.uint16),
+    (256, [1, 2, 200, 255], np.uint8),
+    (5, [4], np.uint8),
+])
+def test_remap_is_the_definition_and_queries_equal_brute_force(universe, alphabet, dtype):
+    """Sparse alphabets: the bitmap marks exactly the codes that occur, S'
+    is each code's rank among them, and access/rank/select through the
+    remapped tree equal direct counting on S, for every argument."""
+    rng = np.random.default_rng(len(alphabet) + universe)
+    S = np.asarray(alphabet, dtype=dtype)[rng.integers(0, len(alphabet), 61)]
+    bm, codes, Sr, sr = O.remap_alphabet(S, universe)
+    present = np.unpackbits(bm, bitorder="little")
+    assert present.shape[0] == ((universe + 511) // 512) * 512
+    assert np.array_equal(np.flatnonzero(present), np.unique(S).astype(np.int64))
+    assert list(codes) == sorted(set(int(x) for x in S))
+    assert sr == len(codes)
+    assert np.array_equal(Sr, np.array([list(codes).index(int(x)) for x in S], np.uint32))
+    bits = O.build_bits(Sr, sr)
+    n = len(S)
+    I = np.arange(n + 2, dtype=np.uint64)
+    want = [int(S[i]) if i < n else 0xFFFFFFFF for i in range(n + 2)]
+    assert list(O.remap_access(codes, bits, n, sr, I)) == want
+    absent = [c for c in range(min(universe, 1200)) if c not in set(alphabet)][:5]
+    for c in list(alphabet) + absent + [universe, universe + 7]:
+        cs = np.full(n + 2, c, np.uint64)
+        r = O.remap_rank(codes, universe, bits, n, sr, cs, I)
+        for i in range(n + 2):
+            w = 2**64 - 1 if c >= universe or i > n else int(np.sum(S[:i] == c))
+            assert int(r[i]) == w, (c, i)
+        occ = np.flatnonzero(S == c) if c < universe else np.zeros(0, np.int64)
+        J = np.arange(len(occ) + 2, dtype=np.uint64)
+        got = O.remap_select(codes, universe, bits, n, sr, np.full(len(J), c, np.uint64), J)
+        for j in range(len(J)):
+            w = int(occ[j - 1]) if 1 <= j <= len(occ) else 2**64 - 1
+            assert int(got[j]) == w, (c, j)
+
+
+def test_remap_of_a_contiguous_alphabet_is_the_identity():
+    S = inputs.uniform(5000, 96, 8, np.uint8)
+    S[:96] = np.arange(96, dtype=np.uint8)   # every code occurs
+    bm, codes, Sr, sr = O.remap_alphabet(S, 96)
+    assert sr == 96 and np.array_equal(codes, np.arange(96)) and np.array_equal(Sr, S.astype(np.uint32))
+    assert np.array_equal(O.build_bits(Sr, sr), O.build_bits(S, 96))
+
+
+def test_remap_edge_cases():
+    bm, codes, Sr, sr = O.remap_alphabet(np.zeros(0, np.uint8), 10)
+    assert len(codes) == 0 and sr == 1 and len(Sr) == 0 and not bm.any()
+    with pytest.raises(O.OracleError):
+        O.remap_alphabet(np.array([3, 10], np.uint8), 10)
