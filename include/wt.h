@@ -125,6 +125,29 @@ wt_handle wt_build_async(const void *S, uint64_t n, uint64_t sigma, int sym_widt
  */
 wt_handle wt_build_matrix_async(const void *S, uint64_t n, uint64_t sigma, int sym_width, void *stream);
 
+/*
+ * The tree of S[0..n) over a non-contiguous alphabet (Section 3: the
+ * construction takes the codes of Sigma contiguous; when they are not, a
+ * bitmap remaps the sequence to a contiguous alphabet).  Codes are in
+ * [0, universe) (universe <= 2^(8 sym_width), else WT_ERR_ARG); the alphabet
+ * bitmap A over [0, universe) marks the codes that occur, sigma' = their
+ * number, and the tree is built over S'[j] = rank1(A, S[j]) in [0, sigma')
+ * with 1, 2 or 4 bytes per code as sigma' needs (wt_info reports sigma =
+ * sigma' and the universe).  wt_access returns the original codes;
+ * wt_rank and wt_select take original codes: a code < universe that does
+ * not occur has rank 0 (i <= n) and no select (UINT64_MAX); a code >=
+ * universe gives UINT64_MAX.  wt_level_view shows the levels of the tree of
+ * S'; wt_alphabet_view shows A (layout and directory of a level of
+ * `universe` bits).  wt_query_multi and wt_merge_async reject such trees.
+ * S may be host or device memory.  The call waits once on stream, after A is
+ * counted, to size the tree; the build itself is then enqueued on stream and
+ * wt_wait completes it.  A symbol >= universe gives WT_ERR_SYMBOL_RANGE (and
+ * NULL) from this call.  Device memory: A with its directory (about
+ * universe / 7 bytes) for the life of the tree, plus n (sym_width + 1..4)
+ * bytes during the build.
+ */
+wt_handle wt_build_remap(const void *S, uint64_t n, uint64_t universe, int sym_width, void *stream);
+
 /* Waits for a handle's build to finish and returns its device-reported status. */
 wt_status wt_wait(wt_handle h);
 
@@ -232,7 +255,8 @@ typedef struct {
     int32_t sym_width;
     int32_t variant;      /* the wt_variant that built it */
     int32_t layout;       /* wt_layout: a wavelet tree or a wavelet matrix */
-    uint64_t device_bytes; /* resident bytes of the tree */
+    uint64_t device_bytes; /* resident bytes of the tree (with its alphabet bitmap, if any) */
+    uint64_t universe;    /* wt_build_remap: the code universe U (sigma is then the alphabet's size); else 0 */
 } wt_info_t;
 
 /* Shape of a built tree (n, sigma, L = ceil(lg sigma) levels of Section
@@ -253,6 +277,11 @@ typedef struct {
 /* Device pointers and sizes of level l (layout above); waits for the build.
  * The pointers stay valid until wt_free. */
 wt_status wt_level_view(wt_handle h, uint32_t l, wt_level_view_t *out);
+
+/* The alphabet bitmap of a tree built by wt_build_remap (layout of a level
+ * of `universe` bits: words, R, Hy, S1, S0, ones = sigma'); WT_ERR_ARG for
+ * other trees.  Waits for the build; pointers valid until wt_free. */
+wt_status wt_alphabet_view(wt_handle h, wt_level_view_t *out);
 
 /*
  * Routes every device allocation of the library through alloc/free_ (for

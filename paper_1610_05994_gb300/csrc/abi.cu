@@ -219,6 +219,12 @@ struct wt_tree {
     bool finalized = false;
     bool matrix = false;  // a wavelet matrix (wt_build_matrix_async)
     wt_status status = WT_OK;
+    // A tree over remapped codes (wt_build_remap): the alphabet bitmap over
+    // [0, universe) with its directory, in alpha_mem.
+    uint64_t universe = 0;
+    LevelDesc alpha{};
+    void *alpha_mem = nullptr;
+    size_t alpha_bytes = 0;
 };
 
 namespace {
@@ -743,6 +749,7 @@ void tree_destroy(wt_tree *t) {
     if (!t) return;
     if (t->done) cudaEventDestroy(t->done);
     if (t->mem) dev_free(t->alloc, t->mem, t->mem_bytes, t->stream);
+    if (t->alpha_mem) dev_free(t->alloc, t->alpha_mem, t->alpha_bytes, t->stream);
     t->batch.reset();  // the batch block goes with its last tree
     delete t;
 }
@@ -1330,7 +1337,7 @@ wt_handle merge_async(const wt_handle *parts, uint32_t k, cudaStream_t st) {
     uint64_t n = 0;
     for (uint32_t a = 0; a < k; a++) {
         if (!parts[a] || parts[a]->sigma != parts[0]->sigma || parts[a]->width != parts[0]->width ||
-            parts[a]->matrix) {
+            parts[a]->matrix || parts[a]->universe) {
             set_last(WT_ERR_ARG);
             return nullptr;
         }
@@ -1376,6 +1383,114 @@ wt_handle merge_async(const wt_handle *parts, uint32_t k, cudaStream_t st) {
 // each built alone into a partial tree, then one merge.  At most two
 // chunks' builds are in flight, so at most two chunks of host symbols are
 // staged on the device at a time.
+// ------------------------------------------------- alphabet remapping
+
+// The tree of S over a non-contiguous alphabet (Section 3): the alphabet
+// bitmap A over [0, universe) marks the codes that occur (remap.cu), the
+// level step's count and scan give A its directory, the host reads
+// sigma' = the ones of A (the one host wait), then S' = rank1(A, S) is built
+// as an ordinary tree over [0, sigma') with the narrowest width that holds
+// sigma' codes.  The handle keeps A for the queries.
+wt_handle build_remap(const void *S, uint64_t n, uint64_t universe, int width, cudaStream_t st) {
+    if (width != 1 && width != 2 && width != 4) return set_last(WT_ERR_ARG), nullptr;
+    if (universe == 0 || universe > (1ull << (8 * width)) || (n > 0 && !S) ||
+        (n > 0 && reinterpret_cast<uintptr_t>(S) % (uintptr_t)width) || n >= (1ull << 56))
+        return set_last(WT_ERR_ARG), nullptr;
+    const Allocator A = current_allocator();
+    // Device copy of host symbols (in stream order on st).
+    const size_t sbytes = n * (uint64_t)width;
+    const void *Sd = S;
+    void *staged = nullptr;
+    if (n > 0 && !is_device_pointer(S)) {
+        staged = dev_alloc(A, sbytes, st);
+        if (!staged) return set_last(WT_ERR_OOM), nullptr;
+        if (cudaMemcpyAsync(staged, S, sbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            dev_free(A, staged, sbytes, st);
+            return set_last(WT_ERR_CUDA), nullptr;
+        }
+        Sd = staged;
+    }
+    // The alphabet block: A's words and directory, then the count and scan
+    // scratch, the error word and the ones count.
+    const Shape sa = shape_of(universe);
+    const size_t cnt_b = align256(lw_counts_bytes(universe, 1)), pre_b = align256(lw_prefix_bytes(universe, 1));
+    const size_t keep = sa.words + sa.R + sa.Hy + 2 * sa.S;
+    const size_t abytes = keep + cnt_b + pre_b + level_job_slot_bytes() + 512;
+    char *am = static_cast<char *>(dev_alloc(A, abytes, st));
+    if (!am) {
+        if (staged) dev_free(A, staged, sbytes, st);
+        return set_last(WT_ERR_OOM), nullptr;
+    }
+    LevelDesc ad{};
+    char *p = am;
+    ad.words = reinterpret_cast<uint32_t *>(p);
+    p += sa.words;
+    ad.R = reinterpret_cast<uint32_t *>(p);
+    p += sa.R;
+    ad.Hy = reinterpret_cast<uint64_t *>(p);
+    p += sa.Hy;
+    ad.S1 = reinterpret_cast<uint32_t *>(p);
+    p += sa.S;
+    ad.S0 = reinterpret_cast<uint32_t *>(p);
+    p += sa.S;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(p);
+    p += cnt_b;
+    uint64_t *pre = reinterpret_cast<uint64_t *>(p);
+    p += pre_b;
+    void *slot = p;
+    p += level_job_slot_bytes();
+    uint32_t *err = reinterpret_cast<uint32_t *>(p);
+    uint64_t *ones = reinterpret_cast<uint64_t *>(p + 256);
+    uint64_t h_ones = 0;
+    uint32_t h_err = 0;
+    wt_status r = WT_OK;
+    if (cudaMemsetAsync(ad.words, 0, sa.nblocks * 64, st) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, 4, st) != cudaSuccess || cudaMemsetAsync(ones, 0, 8, st) != cudaSuccess ||
+        launch_alpha_mark(Sd, n, width, universe, ad.words, err, st) != cudaSuccess ||
+        launch_level_directory(universe, 1, 1, 0, ad, ones, cnt, pre, err, slot, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h_ones, ones, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        r = WT_ERR_CUDA;
+    }
+    if (r == WT_OK && (h_err & kErrSymbol)) r = WT_ERR_SYMBOL_RANGE;
+    if (r == WT_OK && (h_err & kErrTimeout)) r = WT_ERR_TIMEOUT;
+    ad.ones = h_ones;
+    const uint64_t sigma_r = h_ones ? h_ones : 1;  // an empty S still has a tree (of no levels)
+    const int w_r = sigma_r <= 256 ? 1 : (sigma_r <= 65536 ? 2 : 4);
+    wt_tree *t = nullptr;
+    void *mapped = nullptr;
+    const size_t mbytes = n * (uint64_t)w_r;
+    if (r == WT_OK) r = tree_create(n, sigma_r, w_r, st, &t);
+    if (r == WT_OK && n > 0) {
+        mapped = dev_alloc(A, mbytes, st);
+        if (!mapped) r = WT_ERR_OOM;
+        else if (launch_alpha_map(Sd, n, width, ad, mapped, w_r, st) != cudaSuccess) r = WT_ERR_CUDA;
+    }
+    if (r == WT_OK) r = enqueue_build(t, mapped, WT_VARIANT_AUTO, st);
+    if (mapped) dev_free(A, mapped, mbytes, st);
+    if (staged) dev_free(A, staged, sbytes, st);
+    if (r == WT_OK && cudaEventRecord(t->done, st) != cudaSuccess) r = WT_ERR_CUDA;
+    if (r != WT_OK) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        dev_free(A, am, abytes, st);
+        if (t) {
+            t->finalized = true;
+            tree_destroy(t);
+        }
+        return set_last(r), nullptr;
+    }
+    t->universe = universe;
+    t->alpha = ad;
+    t->alpha_mem = am;
+    t->alpha_bytes = abytes;
+    set_last(WT_OK);
+    return t;
+}
+
 wt_handle build_chunked(const void *S, uint64_t n, uint64_t sigma, int width, uint64_t chunk, cudaStream_t st) {
     wt_status r = check_args(S, n, sigma, width);
     if (r == WT_OK && chunk == 0) r = WT_ERR_ARG;
@@ -1463,6 +1578,10 @@ wt_handle wt_build_matrix_async(const void *S, uint64_t n, uint64_t sigma, int s
     return build_async(S, n, sigma, sym_width, WT_VARIANT_LEVELWISE, static_cast<cudaStream_t>(stream), true);
 }
 
+wt_handle wt_build_remap(const void *S, uint64_t n, uint64_t universe, int sym_width, void *stream) {
+    return build_remap(S, n, universe, sym_width, static_cast<cudaStream_t>(stream));
+}
+
 wt_handle wt_merge_async(const wt_handle *parts, uint32_t k, void *stream) {
     return merge_async(parts, k, static_cast<cudaStream_t>(stream));
 }
@@ -1474,8 +1593,10 @@ wt_handle wt_build_chunked(const void *S, uint64_t n, uint64_t sigma, int sym_wi
 wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, void *stream) {
     if (!h || (m && (!i || !out))) return set_last(WT_ERR_ARG);
     ProfScope p(K_Q_ACCESS, 16.0 * m, static_cast<cudaStream_t>(stream));
-    const cudaError_t e = h->matrix ? launch_wm_access(h->d_desc, i, m, out, static_cast<cudaStream_t>(stream))
-                                    : launch_access(h->d_desc, i, m, out, static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = h->matrix      ? launch_wm_access(h->d_desc, i, m, out, st)
+                          : h->universe ? launch_access_remap(h->d_desc, h->alpha, h->universe, i, m, out, st)
+                                        : launch_access(h->d_desc, i, m, out, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_last(WT_ERR_CUDA);
@@ -1486,8 +1607,10 @@ wt_status wt_access(wt_handle h, const uint64_t *i, uint64_t m, uint32_t *out, v
 wt_status wt_rank(wt_handle h, const uint32_t *c, const uint64_t *i, uint64_t m, uint64_t *out, void *stream) {
     if (!h || (m && (!c || !i || !out))) return set_last(WT_ERR_ARG);
     ProfScope p(K_Q_RANK, 16.0 * m, static_cast<cudaStream_t>(stream));
-    const cudaError_t e = h->matrix ? launch_wm_rank(h->d_desc, c, i, m, out, static_cast<cudaStream_t>(stream))
-                                    : launch_rank(h->d_desc, c, i, m, out, static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = h->matrix      ? launch_wm_rank(h->d_desc, c, i, m, out, st)
+                          : h->universe ? launch_rank_remap(h->d_desc, h->alpha, h->universe, c, i, m, out, st)
+                                        : launch_rank(h->d_desc, c, i, m, out, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_last(WT_ERR_CUDA);
@@ -1498,8 +1621,10 @@ wt_status wt_rank(wt_handle h, const uint32_t *c, const uint64_t *i, uint64_t m,
 wt_status wt_select(wt_handle h, const uint32_t *c, const uint64_t *j, uint64_t m, uint64_t *out, void *stream) {
     if (!h || (m && (!c || !j || !out))) return set_last(WT_ERR_ARG);
     ProfScope p(K_Q_SELECT, 16.0 * m, static_cast<cudaStream_t>(stream));
-    const cudaError_t e = h->matrix ? launch_wm_select(h->d_desc, c, j, m, out, static_cast<cudaStream_t>(stream))
-                                    : launch_select(h->d_desc, c, j, m, out, static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = h->matrix      ? launch_wm_select(h->d_desc, c, j, m, out, st)
+                          : h->universe ? launch_select_remap(h->d_desc, h->alpha, h->universe, c, j, m, out, st)
+                                        : launch_select(h->d_desc, c, j, m, out, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_last(WT_ERR_CUDA);
@@ -1514,7 +1639,7 @@ wt_status wt_query_multi(const wt_handle *trees, uint32_t ntrees, const uint32_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::vector<const TreeDesc *> ptrs(ntrees);
     for (uint32_t k = 0; k < ntrees; k++) {
-        if (!trees[k] || trees[k]->matrix) return set_last(WT_ERR_ARG);
+        if (!trees[k] || trees[k]->matrix || trees[k]->universe) return set_last(WT_ERR_ARG);
         ptrs[k] = trees[k]->d_desc;
     }
     const Allocator A = current_allocator();
@@ -1548,7 +1673,27 @@ wt_status wt_info(wt_handle h, wt_info_t *out) {
     out->sym_width = h->width;
     out->variant = h->variant;
     out->layout = h->matrix ? WT_LAYOUT_MATRIX : WT_LAYOUT_TREE;
-    out->device_bytes = h->mem_bytes;
+    out->device_bytes = h->mem_bytes + h->alpha_bytes;
+    out->universe = h->universe;
+    return set_last(h->status);
+}
+
+wt_status wt_alphabet_view(wt_handle h, wt_level_view_t *out) {
+    if (!h || !out || !h->universe) return set_last(WT_ERR_ARG);
+    finalize(h);
+    const Shape s = shape_of(h->universe);
+    const LevelDesc &d = h->alpha;
+    out->words = d.words;
+    out->R = d.R;
+    out->Hy = d.Hy;
+    out->S1 = d.S1;
+    out->S0 = d.S0;
+    out->ones = d.ones;
+    out->n_words = s.nblocks * 16;
+    out->n_R = s.nblocks + 1;
+    out->n_Hy = s.nspans + 1;
+    out->n_S1 = ceil_div(d.ones, kSample);
+    out->n_S0 = ceil_div(h->universe - d.ones, kSample);
     return set_last(h->status);
 }
 

@@ -162,3 +162,82 @@ cudaError_t launch_query_multi(const TreeDesc *const *trees, uint32_t ntrees, co
 }
 
 }  // namespace wt
+
+namespace wt {
+
+// ------------------------------------------------ remapped alphabets
+// A tree built over the remapped codes (remap.cu): the alphabet bitmap A
+// over the universe [0, U) marks the codes that occur; code c is tree symbol
+// rank1(A, c).  access maps the tree's answer r back to select1(A, r + 1);
+// rank and select map c to rank1(A, c) when A[c] = 1.  A code < U that does
+// not occur has rank 0 (for i <= n) and no select; a code >= U gives the
+// sentinel.
+
+__device__ __forceinline__ bool alpha_has(const LevelDesc &A, uint64_t universe, uint64_t c) {
+    return c < universe && bit_at(A, c);
+}
+
+__global__ void __launch_bounds__(kQueryThreads) access_remap_kernel(const TreeDesc *__restrict__ t, LevelDesc A,
+                                                                     uint64_t universe, uint64_t ablocks,
+                                                                     const uint64_t *__restrict__ I, uint64_t m,
+                                                                     uint32_t *__restrict__ out) {
+    const uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const uint32_t r = do_access(*t, I[q]);
+    out[q] = r == UINT32_MAX ? UINT32_MAX : (uint32_t)select_bit(A, universe, ablocks, 1u, (uint64_t)r + 1);
+}
+
+__global__ void __launch_bounds__(kQueryThreads) rank_remap_kernel(const TreeDesc *__restrict__ t, LevelDesc A,
+                                                                   uint64_t universe, const uint32_t *__restrict__ C,
+                                                                   const uint64_t *__restrict__ I, uint64_t m,
+                                                                   uint64_t *__restrict__ out) {
+    const uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const uint64_t c = C[q], i = I[q];
+    uint64_t r;
+    if (c >= universe || i > t->n)
+        r = UINT64_MAX;
+    else if (!bit_at(A, c))
+        r = 0;
+    else
+        r = do_rank(*t, (uint32_t)rank1(A, c), i);
+    out[q] = r;
+}
+
+__global__ void __launch_bounds__(kQueryThreads) select_remap_kernel(const TreeDesc *__restrict__ t, LevelDesc A,
+                                                                     uint64_t universe,
+                                                                     const uint32_t *__restrict__ C,
+                                                                     const uint64_t *__restrict__ J, uint64_t m,
+                                                                     uint64_t *__restrict__ out) {
+    const uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const uint64_t c = C[q];
+    out[q] = alpha_has(A, universe, c) ? do_select(*t, (uint32_t)rank1(A, c), J[q]) : UINT64_MAX;
+}
+
+cudaError_t launch_access_remap(const TreeDesc *t, const LevelDesc &A, uint64_t universe, const uint64_t *i,
+                                uint64_t m, uint32_t *out, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    access_remap_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(t, A, universe, ceil_div(universe, kBlockBits), i, m,
+                                                                out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rank_remap(const TreeDesc *t, const LevelDesc &A, uint64_t universe, const uint32_t *c,
+                              const uint64_t *i, uint64_t m, uint64_t *out, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    rank_remap_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(t, A, universe, c, i, m, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_remap(const TreeDesc *t, const LevelDesc &A, uint64_t universe, const uint32_t *c,
+                                const uint64_t *j, uint64_t m, uint64_t *out, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    select_remap_kernel<<<grid_for(m), kQueryThreads, 0, st>>>(t, A, universe, c, j, m, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace wt

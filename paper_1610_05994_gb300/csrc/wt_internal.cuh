@@ -551,6 +551,21 @@ cudaError_t launch_batch_prepare(const SeqJob *jobs, uint32_t nseq, const uint32
                                  uint32_t nbig, const uint32_t *big_pairs, uint32_t nbig_pairs,
                                  const uint32_t *small_pairs, uint32_t nsmall_pairs, cudaStream_t st);
 
+// Alphabet remapping (remap.cu): mark the codes of S in the alphabet
+// bitmap A (zeroed; codes >= universe set kErrSymbol in err), and map S to
+// S'[j] = rank1(A, S[j]) with out_width bytes per code.
+cudaError_t launch_alpha_mark(const void *S, uint64_t n, int width, uint64_t universe, uint32_t *A, uint32_t *err,
+                              cudaStream_t st);
+cudaError_t launch_alpha_map(const void *S, uint64_t n, int width, const LevelDesc &A, void *out, int out_width,
+                             cudaStream_t st);
+// Queries on a tree of remapped codes (query.cu); A with its directory and ones.
+cudaError_t launch_access_remap(const TreeDesc *t, const LevelDesc &A, uint64_t universe, const uint64_t *i,
+                                uint64_t m, uint32_t *out, cudaStream_t st);
+cudaError_t launch_rank_remap(const TreeDesc *t, const LevelDesc &A, uint64_t universe, const uint32_t *c,
+                              const uint64_t *i, uint64_t m, uint64_t *out, cudaStream_t st);
+cudaError_t launch_select_remap(const TreeDesc *t, const LevelDesc &A, uint64_t universe, const uint32_t *c,
+                                const uint64_t *j, uint64_t m, uint64_t *out, cudaStream_t st);
+
 // Kernel (e): queries.
 cudaError_t launch_access(const TreeDesc *t, const uint64_t *i, uint64_t m, uint32_t *out, cudaStream_t st);
 cudaError_t launch_rank(const TreeDesc *t, const uint32_t *c, const uint64_t *i, uint64_t m, uint64_t *out,

@@ -42,7 +42,8 @@ class _LevelView(C.Structure):
 
 class _Info(C.Structure):
     _fields_ = [("n", C.c_uint64), ("sigma", C.c_uint64), ("levels", C.c_uint32), ("sym_width", C.c_int32),
-                ("variant", C.c_int32), ("layout", C.c_int32), ("device_bytes", C.c_uint64)]
+                ("variant", C.c_int32), ("layout", C.c_int32), ("device_bytes", C.c_uint64),
+                ("universe", C.c_uint64)]
 
 
 class _KernelStat(C.Structure):
@@ -61,6 +62,7 @@ _SIGNATURES = [
     ("wt_build_batch", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
                                  C.c_void_p]),
     ("wt_build_matrix_async", C.c_void_p, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p]),
+    ("wt_build_remap", C.c_void_p, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p]),
     ("wt_merge_async", C.c_void_p, [C.c_void_p, C.c_uint32, C.c_void_p]),
     ("wt_build_chunked", C.c_void_p, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_void_p]),
     ("wt_access", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
@@ -71,6 +73,7 @@ _SIGNATURES = [
     ("wt_free", C.c_int, [C.c_void_p]),
     ("wt_info", C.c_int, [C.c_void_p, C.POINTER(_Info)]),
     ("wt_level_view", C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(_LevelView)]),
+    ("wt_alphabet_view", C.c_int, [C.c_void_p, C.POINTER(_LevelView)]),
     ("wt_set_allocator", C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
     ("wt_last_status", C.c_int, []),
     ("wt_status_string", C.c_char_p, [C.c_int]),
@@ -219,6 +222,36 @@ class Tree:
             t.wait()
         return t
 
+    @classmethod
+    def build_remap(cls, S, universe: int, stream=None, wait: bool = True) -> "Tree":
+        """The tree over a non-contiguous alphabet (wt_build_remap): codes in
+        [0, universe), remapped through the alphabet bitmap to [0, sigma')."""
+        lib = load()
+        if isinstance(S, np.ndarray):
+            S = np.ascontiguousarray(S)
+            width, ptr, n, keep = S.dtype.itemsize, S.ctypes.data, S.size, S
+        else:
+            width, ptr, n, keep = S.element_size(), _dptr(S), S.numel(), S
+        h = lib.wt_build_remap(C.c_void_p(ptr), n, universe, width, C.c_void_p(_stream(stream)))
+        if not h:
+            raise WTError(lib.wt_last_status(), "wt_build_remap")
+        info = _Info()
+        t = cls(h, n, 0, width)
+        t._keep = keep
+        if wait:
+            t.wait()
+        _check(lib.wt_info(t._h, C.byref(info)), "wt_info")
+        t.sigma, t.width = info.sigma, info.sym_width
+        return t
+
+    def alphabet(self) -> LevelView:
+        """Copies of the alphabet bitmap and its directory (wt_build_remap trees)."""
+        v = _LevelView()
+        _check(load().wt_alphabet_view(self._h, C.byref(v)), "wt_alphabet_view")
+        return LevelView(_device_view(v.words, v.n_words, torch.uint32), _device_view(v.R, v.n_R, torch.uint32),
+                         _device_view(v.Hy, v.n_Hy, torch.uint64), _device_view(v.S1, v.n_S1, torch.uint32),
+                         _device_view(v.S0, v.n_S0, torch.uint32), int(v.ones))
+
     def wait(self) -> None:
         _check(load().wt_wait(self._h), "wt_wait")
         self._keep = None
@@ -239,7 +272,8 @@ class Tree:
         out = _Info()
         _check(load().wt_info(self._h, C.byref(out)), "wt_info")
         return {"n": out.n, "sigma": out.sigma, "levels": out.levels, "sym_width": out.sym_width,
-                "variant": out.variant, "layout": out.layout, "device_bytes": out.device_bytes}
+                "variant": out.variant, "layout": out.layout, "device_bytes": out.device_bytes,
+                "universe": out.universe}
 
     def level(self, l: int) -> LevelView:
         """Copies of level l's bitmap words and directories (device tensors)."""
