@@ -812,7 +812,7 @@ def run_batch(args, ws, rank, local):
     B.build_library()
     W.load()
     dev = torch.device("cuda", local)
-    specs = inputs.batch_specs(4096, base=inputs.SEED_BASE + 4 + 1000 * rank)
+    specs = inputs.batch_specs(args.batch_count, base=inputs.SEED_BASE + 4 + 1000 * rank)
     t_gen = time.perf_counter()
     host = _gen_parallel(specs)
     t_gen = time.perf_counter() - t_gen
@@ -906,7 +906,7 @@ def run_batch(args, ws, rank, local):
     line = {"metric": "batched wavelet-tree build symbols/sec", "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8+u16", "data": "synthetic",
-            "config": {"workload": "batch of 4096 sequences, n log-uniform in [2^10, 2^22], sigma in "
+            "config": {"workload": f"batch of {args.batch_count} sequences, n log-uniform in [2^10, 2^22], sigma in "
                                    "{4, 20, 256, 65536} (u8 for sigma <= 256, else u16), uniform or Zipf(1.1)",
                        "symbols_per_step": n_total, "host_generation_s": t_gen,
                        "l2": "inputs (2.6 GB) larger than the 129 MB L2; no flush",
@@ -1081,6 +1081,8 @@ def main():
                "matrix": run_matrix}
     ap.add_argument("--workload", choices=sorted(WORKLOAD_SETS) + sorted(runners), default="text+dna")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured build requests")
+    ap.add_argument("--batch-count", type=int, default=4096,
+                    help="batch: sequences per step (profiling aid; the line then names the count)")
     ap.add_argument("--size-log2", type=int, default=0,
                     help="profiling aid: cap each sequence at 2^k symbols (the line then names the cap)")
     ap.add_argument("--variant", type=int, choices=[0, 1, 2, 3], default=0,
