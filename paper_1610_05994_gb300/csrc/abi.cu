@@ -535,11 +535,10 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
 }
 
 // The wavelet matrix: the level-wise build with one node per level (node
-// tables OB_l = 0, ZE_l = Z_l from matrix.cu).  S_l is ordered by the
-// bit-reversed top l bits, so each top-l key is still one run of S_l and
-// most tiles take the pass's one-run path.  Only level 0's pass hands the
-// next level its bitmap; deeper count passes write the bitmaps from the
-// symbols.
+// tables OB_l = 0, ZE_l = Z_l from matrix.cu).  Every node of a level has
+// the same offsets, so the pass places every tile as one node whatever its
+// keys (one_node), and each level's pass hands the next level its bitmap
+// (1- and 2-byte codes; the last level then needs no symbols).
 wt_status enqueue_matrix(wt_tree *t, const void *S, cudaStream_t st) {
     Scratch sc;
     wt_status r = scratch_alloc(t->alloc, sc, t->n, t->sigma, t->L, t->width, true, st);
@@ -549,7 +548,7 @@ wt_status enqueue_matrix(wt_tree *t, const void *S, cudaStream_t st) {
     const uint32_t R = hist_replicas(t->n, t->sigma);
     const uint64_t ntiles = ceil_div(t->n, lw_tile_elems(t->width));
     const bool fuse0 = !R && t->L > 0 && level0_fusable(S, t->n, t->width, t->sigma);
-    const bool next0 = t->L > 1 && pass_writes_next_bits(0, ntiles, t->width);
+    const bool next0 = t->L > 1 && pass_writes_next_bits(0, ntiles, t->width);  // no boundaries: one node
     {
         ProfScope p(K_HIST, nw, st);
         if (R) {
@@ -580,13 +579,15 @@ wt_status enqueue_matrix(wt_tree *t, const void *S, cudaStream_t st) {
         void *bufs[2] = {b.ping, b.pong};
         bool from_bits = false;
         for (uint32_t l = 0; l < t->L; l++) {
-            void *nxt = (l + 1 < t->L) ? bufs[l & 1] : nullptr;
-            const bool next_bits = nxt && l == 0 && next0;
-            ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, nxt != nullptr), st);
+            const bool has_next = l + 1 < t->L;
+            const bool next_bits = has_next && next0;
+            const bool store = has_next && !(l + 2 == t->L && next_bits);
+            void *nxt = store ? bufs[l & 1] : nullptr;
+            ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, has_next), st);
             WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
                                     &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
                                     next_bits ? t->h_desc.lv[l + 1].words : nullptr, t->d_err, b.job_slot, st,
-                                    l == 0 && fuse0));
+                                    l == 0 && fuse0, nullptr, 0, true));
             from_bits = next_bits;
             cur = nxt;
         }

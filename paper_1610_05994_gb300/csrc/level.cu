@@ -448,7 +448,8 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     const uint32_t shv = J.L - l;  // key_l = s >> shv
     const uint32_t nodes = 1u << l;
     const Sym *sb = reinterpret_cast<const Sym *>(buf);
-    const uint32_t kfirst = (uint32_t)sb[0] >> shv, klast = (uint32_t)sb[cnt - 1] >> shv;
+    const uint32_t kfirst = a.one_node ? 0u : (uint32_t)sb[0] >> shv;
+    const uint32_t klast = a.one_node ? 0u : (uint32_t)sb[cnt - 1] >> shv;
     Sym *nxt = static_cast<Sym *>(J.nxt);
     if (kfirst == klast && kfirst < nodes) {
         gz = (base - P) + __ldg(J.ob + kfirst);  // first zero's position in P_{l+1}
@@ -754,9 +755,9 @@ LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint3
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
                               uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
                               uint32_t *err, cudaStream_t st, bool counted, const RankTables *rt,
-                              uint32_t check_sigma) {
+                              uint32_t check_sigma, bool one_node) {
     if (njobs == 0 || total_tiles == 0) return cudaSuccess;
-    LevelLaunch a;
+    LevelLaunch a{};
     a.jobs = jobs;
     a.tile_start = tile_start;
     a.njobs = njobs;
@@ -768,6 +769,7 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.err = err;
     a.ways = 1;
     a.check_sigma = check_sigma;
+    a.one_node = one_node;
     switch (width) {
         case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, counted, st, rt);
         case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, counted, st, rt);
@@ -859,7 +861,8 @@ cudaError_t launch_level_directory(uint64_t n, int width, uint32_t L, uint32_t l
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
                               uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
-                              cudaStream_t st, bool counted, const RankTables *rt, uint32_t check_sigma) {
+                              cudaStream_t st, bool counted, const RankTables *rt, uint32_t check_sigma,
+                              bool one_node) {
     if (n == 0) return cudaSuccess;
     const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, cnt, pre, next_words);
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
@@ -869,7 +872,7 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, from_bits, l + 1 < L, err, st, counted, rt,
-                             check_sigma);
+                             check_sigma, one_node);
 }
 
 }  // namespace wt

@@ -56,6 +56,7 @@ struct LevelLaunch {
     uint32_t *err;
     uint32_t ways;               // count arrays the scan turns into prefixes (1, or 3 for a pair step)
     uint32_t check_sigma;        // > 0: the count pass from the symbols flags any symbol >= check_sigma
+    uint32_t one_node;           // every node has the same offsets: each tile is placed as node 0
 };
 
 // Whether some symbol of a 16-byte chunk is >= sigma (sigma >= 1).  For bytes

@@ -462,13 +462,15 @@ struct RankTables {
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
                               uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
                               uint32_t *err, cudaStream_t st, bool counted = false, const RankTables *rt = nullptr,
-                              uint32_t check_sigma = 0);
+                              uint32_t check_sigma = 0, bool one_node = false);
 // One sequence (job_slot: level_job_slot_bytes() of device memory).
+// one_node: every node of level l has the same offsets (the wavelet
+// matrix), so every tile is placed as one node whatever its keys.
 cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width, uint32_t L, uint32_t l,
                               const uint64_t *ob, const uint64_t *ze, LevelDesc lv, uint64_t *ones_out, uint32_t *cnt,
                               uint64_t *pre, bool from_bits, uint32_t *next_words, uint32_t *err, void *job_slot,
                               cudaStream_t st, bool counted = false, const RankTables *rt = nullptr,
-                              uint32_t check_sigma = 0);
+                              uint32_t check_sigma = 0, bool one_node = false);
 
 // The prefix scan alone of level l (ways count arrays, way 0 with the
 // directory), over jobs already in device memory.
