@@ -822,8 +822,12 @@ def run_batch(args, ws, rank, local):
     st = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
 
+    host_ms = []  # host time of each wt_build_batch call (plan, uploads, graph capture and launch)
+
     def step(keep):
+        h0 = time.perf_counter()
         trees = W.build_batch(seqs, sigmas, stream=st, wait=False)
+        host_ms.append((time.perf_counter() - h0) * 1e3)
         with torch.cuda.stream(st):
             for t in keep:
                 t.free()
@@ -912,6 +916,7 @@ def run_batch(args, ws, rank, local):
                        "l2": "inputs (2.6 GB) larger than the 129 MB L2; no flush",
                        "parallelism": f"replicas{ws}"},
             "batch_efficiency_vs_plain": efficiency,
+            "host_ms_per_call": float(np.median(host_ms[args.warmup:] or host_ms)),
             "plain_rate_per_class": {f"sigma={k[0]} w={k[1]} {k[2]}": v for k, v in rate.items()},
             "roofline": roofline, "cpu_baseline": None,
             "e2e": {"value": job_rate(n_total, ws, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -923,20 +928,59 @@ def run_batch(args, ws, rank, local):
 SERVE_POOL_N = 1 << 26
 
 
+def _serve_phase(srv, BuildRequest, specs, offs, pools, hists, lam, warm, rng, qrng, arrive):
+    """Runs one serving phase: Poisson arrivals at rate lam, the server's
+    steps, and closed-loop query batches on the resident trees.  Returns the
+    measured requests (rid >= warm), the measured query batches and the
+    phase's wall time."""
+    import torch
+
+    total = len(specs)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, total))
+    where = {}  # rid -> (sigma, offset, n)
+    qbs = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = 0
+    qb = None
+    while len(srv.finished) + len(srv.failed) + len(srv.rejected) < total:
+        now = time.perf_counter() - t0
+        while k < total and arrivals[k] <= now:
+            where[k] = (specs[k].sigma, offs[k], specs[k].n)
+            srv.submit(BuildRequest(k, arrive(k), specs[k].sigma, t0 + arrivals[k]))
+            k += 1
+        srv.step()
+        srv.poll_queries()
+        if srv.resident and (qb is None or qb.done):
+            rids = list(srv.resident)
+            tidx, op, c, arg = _serve_queries(qrng, rids, where, pools, hists, QUERIES)
+            q = [torch.from_numpy(x).to(srv.device, non_blocking=False) for x in (tidx, op, c, arg)]
+            qb = srv.query([srv.resident[r][0] for r in rids], *q)
+            qb.measured = k > warm
+            qbs.append(qb)
+    srv.drain()
+    meas = [r for r in srv.finished if r.rid >= warm]
+    q_meas = [q for q in qbs if getattr(q, "measured", False) and q.done]
+    return meas, q_meas, time.perf_counter() - t0
+
+
 def run_serve(args, ws, rank, local):
     """Serving loop: Poisson arrivals of build requests at an offered load of
     70% of the measured batched build rate, continuous batching under a 120 GB
-    budget, closed-loop batches of 2^16 mixed queries on the resident trees."""
+    budget, closed-loop batches of 2^16 mixed queries on the resident trees.
+    A second phase offers requests until the resident trees reach the budget,
+    so that admission evicts the oldest trees."""
     import torch
 
     from paper_1610_05994_gb300 import build as B
     from paper_1610_05994_gb300 import wt as W
-    from paper_1610_05994_gb300.serve import BuildRequest, Server, percentiles
+    from paper_1610_05994_gb300.serve import BuildRequest, Server, percentiles, resident_bytes
 
     torch.cuda.set_device(local)
     B.build_library()
     W.load()
     dev = torch.device("cuda", local)
+    budget = 120 << 30
     warm, total = 100, 100 + args.requests
     specs = inputs.serving_specs(total, base=inputs.SEED_BASE + 5 + 1000 * rank)
     # Request data: slices of one pinned Zipf(1.0) pool per alphabet, at
@@ -949,59 +993,50 @@ def run_serve(args, ws, rank, local):
     rng = np.random.default_rng(55 + rank)
     offs = [int(rng.integers(0, SERVE_POOL_N - sp.n + 1)) for sp in specs]
 
-    def arrive(k):
-        sp = specs[k]
-        S = torch.empty(sp.n, dtype=pools[sp.sigma].dtype, device=dev)
-        S.copy_(pools[sp.sigma][offs[k]:offs[k] + sp.n], non_blocking=True)
-        return S
+    def arriver(sp_list, off_list):
+        def arrive(k):
+            sp = sp_list[k]
+            S = torch.empty(sp.n, dtype=pools[sp.sigma].dtype, device=dev)
+            S.copy_(pools[sp.sigma][off_list[k]:off_list[k] + sp.n], non_blocking=True)
+            return S
+        return arrive
 
-    # Calibration: the batched build rate on 64 requests of this distribution.
+    arrive = arriver(specs, offs)
+    # Calibration on 64 requests of this distribution: the batched build
+    # rate (one wt_build_batch call) and the plain rate (each request built
+    # alone, one after the other).
     cal = [arrive(k) for k in range(64)]
+    cal_sig = [specs[k].sigma for k in range(64)]
+    cal_n = sum(specs[k].n for k in range(64))
     for _ in range(2):
-        for t in W.build_batch(cal, [specs[k].sigma for k in range(64)]):
+        for t in W.build_batch(cal, cal_sig):
             t.free()
+        for S, sg in zip(cal, cal_sig):
+            W.Tree.build(S, sg).free()
     torch.cuda.synchronize()
     c0 = time.perf_counter()
-    for t in W.build_batch(cal, [specs[k].sigma for k in range(64)]):
+    for t in W.build_batch(cal, cal_sig):
         t.free()
     torch.cuda.synchronize()
-    batch_rate = sum(specs[k].n for k in range(64)) / (time.perf_counter() - c0)
+    batch_rate = cal_n / (time.perf_counter() - c0)
+    c0 = time.perf_counter()
+    for S, sg in zip(cal, cal_sig):
+        W.Tree.build(S, sg, wait=False).free()
+    torch.cuda.synchronize()
+    plain_rate = cal_n / (time.perf_counter() - c0)
     del cal
     mean_n = float(np.mean([sp.n for sp in specs]))
     lam = 0.7 * batch_rate / mean_n
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, total))
 
-    srv = Server(budget_bytes=120 << 30, max_batch=1024, device=dev)
-    where = {}  # rid -> (sigma, offset, n)
-    qbs = []
+    # Phase 1: the measured serving run.
+    srv = Server(budget_bytes=budget, max_batch=1024, device=dev)
     qrng = np.random.default_rng(77 + rank)
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     W.profile_begin()
-    t0 = time.perf_counter()
-    k = 0
-    qb = None
-    while len(srv.finished) < total:
-        now = time.perf_counter() - t0
-        while k < total and arrivals[k] <= now:
-            where[k] = (specs[k].sigma, offs[k], specs[k].n)
-            srv.submit(BuildRequest(k, arrive(k), specs[k].sigma, t0 + arrivals[k]))
-            k += 1
-        srv.step()
-        srv.poll_queries()
-        if srv.resident and (qb is None or qb.done):
-            rids = list(srv.resident)
-            tidx, op, c, arg = _serve_queries(qrng, rids, where, pools, hists, QUERIES)
-            q = [torch.from_numpy(x).to(dev, non_blocking=False) for x in (tidx, op, c, arg)]
-            qb = srv.query([srv.resident[r][0] for r in rids], *q)
-            qb.measured = k > warm
-            qbs.append(qb)
-    srv.drain()
-    t_end = time.perf_counter()
+    meas, qbs, wall = _serve_phase(srv, BuildRequest, specs, offs, pools, hists, lam, warm, rng, qrng, arrive)
     stats = W.profile_end()
     clk = clocks.stop()
-    meas = [r for r in srv.finished if r.rid >= warm]
     first = min(r.arrival for r in meas)
     last = max(r.done for r in meas)
     # replicas: every rank serves its own stream; the job's rate is all the
@@ -1009,9 +1044,32 @@ def run_serve(args, ws, rank, local):
     span_s = reduce_max(last - first, ws)
     value = reduce_sum(sum(r.n for r in meas), ws) / span_s
     build_lat = [(r.done - r.arrival) * 1e3 for r in meas]
-    q_lat = [(q.done - q.issued) * 1e3 for q in qbs if getattr(q, "measured", False) and q.done]
-    evicted = srv.evicted
+    wait_lat = [(r.admitted - r.arrival) * 1e3 for r in meas]
+    q_lat = [(q.done - q.issued) * 1e3 for q in qbs]
+    phase1 = {"evicted": srv.evicted, "peak_used_gb": srv.peak_used / 2**30, "build_batches": srv.batches,
+              "batch_host_ms": percentiles(srv.batch_host_ms), "rejected": len(srv.rejected),
+              "failed": len(srv.failed)}
     srv.close()
+
+    # Phase 2, at the budget: enough requests that the resident trees fill
+    # the 120 GB and admission evicts the oldest ones.
+    mean_keep = float(np.mean([resident_bytes(sp.n, sp.sigma) for sp in specs]))
+    total2 = int(1.3 * budget / mean_keep) + warm
+    specs2 = inputs.serving_specs(total2, base=inputs.SEED_BASE + 6 + 1000 * rank)
+    offs2 = [int(rng.integers(0, SERVE_POOL_N - sp.n + 1)) for sp in specs2]
+    srv2 = Server(budget_bytes=budget, max_batch=1024, device=dev)
+    meas2, qbs2, wall2 = _serve_phase(srv2, BuildRequest, specs2, offs2, pools, hists, lam, warm, rng, qrng,
+                                      arriver(specs2, offs2))
+    first2 = min(r.arrival for r in meas2)
+    last2 = max(r.done for r in meas2)
+    at_cap = {"requests": total2 - warm, "value": sum(r.n for r in meas2) / (last2 - first2), "unit": UNIT,
+              "evicted": srv2.evicted, "peak_used_gb": srv2.peak_used / 2**30, "budget_gb": budget / 2**30,
+              "rejected": len(srv2.rejected), "failed": len(srv2.failed), "build_batches": srv2.batches,
+              "latency_ms": {"build": percentiles([(r.done - r.arrival) * 1e3 for r in meas2]),
+                             "admission_wait": percentiles([(r.admitted - r.arrival) * 1e3 for r in meas2]),
+                             "query_batch": percentiles([(q.done - q.issued) * 1e3 for q in qbs2])},
+              "batch_host_ms": percentiles(srv2.batch_host_ms), "wall_s": wall2}
+    srv2.close()
     if rank != 0:
         return
     roofline, kernels, launches = roofline_of(stats, 1)
@@ -1023,12 +1081,15 @@ def run_serve(args, ws, rank, local):
                                    "{256 (u8), 65536 (u16)}, Zipf(1.0); closed-loop batches of 2^16 mixed "
                                    "access/rank/select queries on resident trees; 120 GB admission budget",
                        "requests": args.requests, "warmup_requests": warm, "offered_load": 0.7,
-                       "calibrated_batch_rate": batch_rate, "arrival_rate_per_s": lam,
-                       "parallelism": f"replicas{ws}"},
-            "latency_ms": {"build": percentiles(build_lat), "query_batch": percentiles(q_lat)},
+                       "calibrated_batch_rate": batch_rate, "calibrated_plain_rate": plain_rate,
+                       "arrival_rate_per_s": lam, "parallelism": f"replicas{ws}"},
+            "served_vs_batch_rate": value / batch_rate, "served_vs_plain_rate": value / plain_rate,
+            "batch_vs_plain_rate": batch_rate / plain_rate,
+            "latency_ms": {"build": percentiles(build_lat), "admission_wait": percentiles(wait_lat),
+                           "query_batch": percentiles(q_lat)},
             "queries_per_s": QUERIES * len(q_lat) / (last - first) if q_lat else None,
-            "query_batches": len(q_lat), "build_batches": srv.batches, "evicted": evicted,
-            "wall_s": t_end - t0, "roofline": roofline, "cpu_baseline": None,
+            "query_batches": len(q_lat), **phase1, "at_capacity": at_cap,
+            "wall_s": wall, "roofline": roofline, "cpu_baseline": None,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": float(np.mean(
                         [specs[r.rid].n * specs[r.rid].width for r in meas])), "d2h_bytes_per_step": 0,
                     "note": "the value itself is end to end: request data is copied from pinned host "

@@ -48,14 +48,19 @@ class QueryBatch:
     done: float = 0.0
 
 
-def tree_bytes(n: int, sigma: int, width: int) -> int:
-    """Device bytes a build of n symbols holds: the tree (bitmaps plus
-    directories, about 1.07 n bits per level) and its transient scratch (two
-    order buffers, histogram and node tables)."""
+def resident_bytes(n: int, sigma: int) -> int:
+    """Device bytes a built tree of n symbols keeps: its bitmaps plus
+    directories, about 1.07 n bits per level."""
     L = max(0, (sigma - 1).bit_length())
-    tree = L * (n // 8 + n // 128 + n // 1024 + 4096)
+    return L * (n // 8 + n // 128 + n // 1024 + 4096)
+
+
+def tree_bytes(n: int, sigma: int, width: int) -> int:
+    """Device bytes a build of n symbols holds while it runs: the tree and
+    its transient scratch (two order buffers, histogram and node tables)."""
+    L = max(0, (sigma - 1).bit_length())
     scratch = 2 * n * width + (1 << L) * 32 + sigma * 8 + L * (n // 512 + 64)
-    return tree + scratch
+    return resident_bytes(n, sigma) + scratch
 
 
 class Server:
@@ -69,6 +74,8 @@ class Server:
         self.inflight: list = []                  # (requests, trees, event)
         self.resident: OrderedDict = OrderedDict()  # rid -> (tree, bytes, request)
         self.used = 0
+        self.peak_used = 0
+        self.batch_host_ms: list[float] = []      # host time of each wt_build_batch call
         self.finished: list[BuildRequest] = []
         self.failed: list[BuildRequest] = []     # builds whose wait raised (their bytes are given back)
         self.rejected: list[BuildRequest] = []   # requests larger than the whole budget
@@ -114,6 +121,7 @@ class Server:
                 break
             self.queue.popleft()
             self.used += need
+            self.peak_used = max(self.peak_used, self.used)
             req.admitted = time.perf_counter()
             batch.append((req, need))
         if not batch:
@@ -122,7 +130,9 @@ class Server:
         self.build_stream.wait_stream(torch.cuda.current_stream(self.device))
         for r in reqs:
             r.S.record_stream(self.build_stream)
+        h0 = time.perf_counter()
         trees = W.build_batch([r.S for r in reqs], [r.sigma for r in reqs], stream=self.build_stream, wait=False)
+        self.batch_host_ms.append((time.perf_counter() - h0) * 1e3)
         ev = torch.cuda.Event()
         ev.record(self.build_stream)
         self.inflight.append((batch, trees, ev))
@@ -151,7 +161,10 @@ class Server:
                     continue
                 req.done = now
                 self.finished.append(req)
-                self.resident[req.rid] = (tree, need, req)
+                # The build's scratch is freed: the tree keeps its own bytes.
+                keep = resident_bytes(req.n, req.sigma)
+                self.used -= need - keep
+                self.resident[req.rid] = (tree, keep, req)
                 self.built_symbols += req.n
         self.inflight = still
 

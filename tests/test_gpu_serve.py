@@ -18,7 +18,9 @@ def test_serving_results_equal_alone():
     rng = np.random.default_rng(11)
     specs = inputs.serving_specs(40, log2_min=10, log2_max=17)
     seqs = [sp.generate() for sp in specs]
-    srv = Server(budget_bytes=24 << 20, max_batch=8)
+    # 3.5 MB: above the largest build's need (2.9 MB with its scratch), below
+    # that plus the trees left resident (2.8 MB in all), so admission evicts.
+    srv = Server(budget_bytes=7 << 19, max_batch=8)
     issued = []  # (query batch, [rid per tree], tidx, op, c, arg)
     nxt = 0
     for round_ in range(60):
