@@ -187,9 +187,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# The sources of the level step's kernels (count, scans, rank tables, pass):
+# the DRAM traffic recorded in profiles/traffic.json holds while they are
+# unchanged.
+LEVEL_STEP_SOURCES = ("level.cu", "level_common.cuh", "wt_internal.cuh", "build.cu")
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1610_05994_gb300", "csrc"))):
+    for f in LEVEL_STEP_SOURCES:
         with open(os.path.join(ROOT, "paper_1610_05994_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
