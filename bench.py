@@ -201,9 +201,13 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+RUN = {"workload": None, "size_log2": None, "variant": 0}  # what this invocation measures
+
+
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+    was taken on the current kernel sources for this invocation's workload at
+    full size; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -211,6 +215,8 @@ def ncu_traffic(kernel: str):
     except (OSError, ValueError):
         return None
     if not rec or rec.get("source_hash") != source_hash():
+        return None
+    if rec.get("workload") != RUN["workload"] or RUN["size_log2"] or RUN["variant"] not in (0, 1):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -1167,6 +1173,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
+        RUN.update(workload=args.workload, size_log2=args.size_log2, variant=args.variant)
         runners.get(args.workload, run_ours)(args, ws, rank, local)
     finally:
         if ws > 1:
