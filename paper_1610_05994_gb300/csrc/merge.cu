@@ -12,17 +12,17 @@
 //
 // Bits.  Level l of the result holds, node by node, the parts' runs of that
 // node in part order: Algorithm 2's global offsets, node-major and
-// part-minor.  A thread writes 128 consecutive bits of the result with one
-// 16-byte store.  It finds the node that holds its first bit by binary
-// search over the result's node starts and the part by walking that node's
-// runs.  A group inside one run is a funnel shift of five source words;
-// otherwise the thread copies pieces of at most 32 bits (one or two source
-// words each, never crossing an output word) until its 128 bits are done,
-// moving to the next part's run and, when a node is exhausted, searching
-// again.  Where
-// mergeBA writes each run's boundary words atomically, here every output
-// word has exactly one writer: no atomics, and the padding bits beyond n are
-// written as zeros by the same stores.
+// part-minor.  A thread writes groups of 128 consecutive bits of the result,
+// one 16-byte store each.  It finds the run (part a of node v) that holds a
+// group's first bit by binary search over the result's node starts and a
+// walk over that node's parts, and keeps it for its next group, where it
+// usually still holds.  A group inside one run is a funnel shift of five
+// source words; otherwise the thread copies pieces of at most 32 bits (one or
+// two source words each, never crossing an output word) until its 128 bits
+// are done, moving to the next part's run and, when a node is exhausted,
+// searching again.  Where mergeBA writes each run's boundary words
+// atomically, here every output word has exactly one writer: no atomics, and
+// the padding bits beyond n are written as zeros by the same stores.
 //
 // The directory of each merged level (R, Hy, S1, S0 and its ones) comes from
 // the level step's count-from-bitmap and scan kernels (createRankSelect).
@@ -139,56 +139,80 @@ __device__ __forceinline__ bool merge_locate(const MergeLevel &m, uint64_t v, ui
     return false;
 }
 
+// The node of the result that holds bit pos: the last v with Hex[v << s] <= pos.
+__device__ __forceinline__ uint64_t merge_node(const MergeLevel &m, uint32_t s, uint64_t pos) {
+    uint64_t lo = 0, hi = (1ull << m.l) - 1;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (m.hexm[mid << s] <= pos)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// A warp takes kMergeRun consecutive 32-group blocks; lane i writes group i of
+// each (so every store instruction covers 512 consecutive bytes) and keeps
+// the part run that held its last bit: the next group, 4096 bits on, usually
+// lies in the same run, and the node search is taken only where a run ends.
+constexpr uint32_t kMergeRun = 8;
+
 __global__ void __launch_bounds__(kMergeThreads) merge_level_kernel(MergeLevel m) {
     const uint32_t s = m.L - m.l;
-    const uint64_t last = (1ull << m.l) - 1;  // the last node
     const uint64_t stride = (1ull << m.L) + 1;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    const uint64_t blocks = ceil_div(m.groups, 32ull * kMergeRun);  // warp work units
     bool bad = false;
-    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < m.groups;
-         g += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
-        uint64_t pos = g * 128;
-        const uint64_t end = min(pos + 128, m.n);
-        while (pos < end) {
-            // The node holding bit pos: the last v with Hex[v << s] <= pos.
-            uint64_t lo = 0, hi = last;
-            while (lo < hi) {
-                const uint64_t mid = (lo + hi + 1) >> 1;
-                if (m.hexm[mid << s] <= pos)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            const uint64_t v = lo;
-            uint32_t a;
-            uint64_t d, src, len;
-            if (!merge_locate(m, v, s, pos, a, d, src, len)) {
-                bad = true;
-                break;
-            }
-            const TreeDesc *P = m.parts[a];
-            const uint32_t *sw = P->lv[m.l].words;
-            uint64_t pn = P->n;
-            if (end - pos == 128 && d + len - pos >= 128) {
-                // The whole group lies in one run: a funnel shift of five
-                // consecutive source words.
-                const uint64_t sp = src + (pos - d);
-                if (sp >= pn || pn - sp < 128) {
-                    bad = true;
+    for (uint64_t u = blockIdx.x * (uint64_t)(blockDim.x / 32) + (threadIdx.x >> 5); u < blocks && !bad;
+         u += warps) {
+        // The part run (part a of node v) that holds the lane's current bit:
+        // result bits [d, d + len) from the part's bits [src, src + len).
+        bool have = false;
+        uint64_t v = 0, d = 0, src = 0, len = 0, pn = 0;
+        uint32_t a = 0;
+        const uint32_t *sw = nullptr;
+        for (uint32_t j = 0; j < kMergeRun && !bad; j++) {
+            const uint64_t g = (u * kMergeRun + j) * 32 + lane;
+            if (g >= m.groups) break;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            uint64_t pos = g * 128;
+            const uint64_t end = min(pos + 128, m.n);
+            while (pos < end) {
+                if (!have || pos < d || pos >= d + len) {
+                    v = merge_node(m, s, pos);
+                    if (!merge_locate(m, v, s, pos, a, d, src, len)) {
+                        bad = true;
+                        break;
+                    }
+                    const TreeDesc *P = m.parts[a];
+                    sw = P->lv[m.l].words;
+                    pn = P->n;
+                    have = true;
+                }
+                if (end - pos == 128 && d + len - pos >= 128) {
+                    // The whole group lies in one run: a funnel shift of five
+                    // consecutive source words.
+                    const uint64_t sp = src + (pos - d);
+                    if (sp >= pn || pn - sp < 128) {
+                        bad = true;
+                        break;
+                    }
+                    const uint32_t so = (uint32_t)(sp & 31);
+                    const uint32_t *q = sw + (sp >> 5);
+                    const uint32_t x0 = __ldg(q), x1 = __ldg(q + 1), x2 = __ldg(q + 2), x3 = __ldg(q + 3);
+                    const uint32_t x4 = so ? __ldg(q + 4) : 0u;
+                    w[0] = __funnelshift_r(x0, x1, so);
+                    w[1] = __funnelshift_r(x1, x2, so);
+                    w[2] = __funnelshift_r(x2, x3, so);
+                    w[3] = __funnelshift_r(x3, x4, so);
+                    pos = end;
                     break;
                 }
-                const uint32_t so = (uint32_t)(sp & 31);
-                const uint32_t *q = sw + (sp >> 5);
-                const uint32_t x0 = __ldg(q), x1 = __ldg(q + 1), x2 = __ldg(q + 2), x3 = __ldg(q + 3);
-                const uint32_t x4 = so ? __ldg(q + 4) : 0u;
-                w[0] = __funnelshift_r(x0, x1, so);
-                w[1] = __funnelshift_r(x1, x2, so);
-                w[2] = __funnelshift_r(x2, x3, so);
-                w[3] = __funnelshift_r(x3, x4, so);
-                break;
-            }
-            bool node_done = false;
-            while (pos < end && !node_done) {
+                // Pieces of at most 32 bits (one or two source words each,
+                // never crossing an output word) up to the group's or the
+                // run's end.
                 const uint32_t off = (uint32_t)(pos & 31);
                 uint64_t cnt = 32 - off;
                 if (d + len - pos < cnt) cnt = d + len - pos;
@@ -196,7 +220,6 @@ __global__ void __launch_bounds__(kMergeThreads) merge_level_kernel(MergeLevel m
                 const uint64_t sp = src + (pos - d);  // the piece's first source bit
                 if (sp >= pn || pn - sp < cnt) {
                     bad = true;
-                    pos = end;
                     break;
                 }
                 const uint32_t so = (uint32_t)(sp & 31);
@@ -208,8 +231,9 @@ __global__ void __launch_bounds__(kMergeThreads) merge_level_kernel(MergeLevel m
 #pragma unroll
                 for (int q = 0; q < 4; q++) w[q] |= wi == (uint32_t)q ? piece : 0u;
                 pos += cnt;
-                if (pos < end && pos == d + len) {
-                    // The next part's run of node v, skipping empty ones.
+                if (pos == d + len) {
+                    // The next part's run of node v, skipping empty ones; past
+                    // the node's last part the next bit is searched again.
                     d += len;
                     len = 0;
                     for (a++; a < m.k; a++) {
@@ -219,17 +243,17 @@ __global__ void __launch_bounds__(kMergeThreads) merge_level_kernel(MergeLevel m
                         if (len) break;
                     }
                     if (a < m.k) {
-                        P = m.parts[a];
+                        const TreeDesc *P = m.parts[a];
                         sw = P->lv[m.l].words;
                         pn = P->n;
                     } else {
-                        node_done = true;  // search the node of pos again
+                        have = false;
                     }
                 }
             }
             if (bad) break;
+            reinterpret_cast<uint4 *>(m.words)[g] = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        reinterpret_cast<uint4 *>(m.words)[g] = make_uint4(w[0], w[1], w[2], w[3]);
     }
     if (bad) atomicOr(m.err, kErrBound);
 }
@@ -262,7 +286,7 @@ cudaError_t launch_merge_level(const TreeDesc *const *parts, uint32_t k, uint32_
     m.L = L;
     m.l = l;
     if (m.groups == 0) return cudaSuccess;
-    merge_level_kernel<<<merge_grid(m.groups, 8), kMergeThreads, 0, st>>>(m);
+    merge_level_kernel<<<merge_grid(ceil_div(m.groups, kMergeRun), 8), kMergeThreads, 0, st>>>(m);
     note_launches(1);
     return cudaGetLastError();
 }
