@@ -77,8 +77,10 @@ size_t lw_prefix_bytes(uint64_t n, int width) {
 //     bits as level l's bitmap;
 //   kFromBits = true: level l's bitmap was written by the pass of level
 //     l - 1; popcount it (n/8 bytes instead of n w).
-// Both zero the tile's range of level l + 1's bitmap when this level's pass
-// will write it (J.next_words), which the pass's boundary words need.
+// (When this level's pass will write level l + 1's bitmap, J.next_words,
+// scan_segs_kernel zeroes that bitmap's padding beyond n; the pass writes
+// every bit below n: whole words by plain stores, words shared by runs
+// bit-exactly by atomics.)
 constexpr int kCountThreads = 256;
 constexpr int kCountWarps = kCountThreads / 32;
 
@@ -173,16 +175,6 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
                     }
             }
         }
-        if (J.next_words) {
-            // Zero level l + 1's bitmap over the same positions (16-byte stores).
-            constexpr uint32_t kVec4 = kTileWords / 4;
-            uint4 *nw = reinterpret_cast<uint4 *>(J.next_words + w0);
-#pragma unroll
-            for (uint32_t r = 0; r < (kVec4 + 31) / 32; r++) {
-                const uint32_t i = r * 32 + lane;
-                if (i < kVec4 && w0 + 4ull * i < nwords) nw[i] = make_uint4(0u, 0u, 0u, 0u);
-            }
-        }
         uint32_t mine = 0;  // lane j < kU stores unit j's count
 #pragma unroll
         for (int j = 0; j < (int)kU; j++) {
@@ -233,6 +225,11 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     const uint32_t nt = J.ntiles * a.units;  // units
     if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) return;
     const uint32_t way = blockIdx.y;
+    if (way == 0 && seg == 0 && J.next_words && threadIdx.x < 32) {
+        // Level l + 1's padding beyond n (the rest of its last 512-bit
+        // block), which the pass leaves alone.
+        for (uint64_t w = J.n / 32 + threadIdx.x; w < J.nblocks * 16; w += 32) J.next_words[w] = 0u;
+    }
     const uint32_t *cnt = J.cnt + way * way_cnt_stride(nt);
     uint64_t *pre = J.pre + way * way_pre_stride(nt);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -519,7 +516,12 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                     const uint64_t dst = bit ? P + ob + __ldg(J.ze + v) : (base + p - P - ob) + __ldg(J.ob + v);
                     if (dst < J.n) {
                         if (nxt) nxt[dst] = (Sym)sv;
-                        if (next_words && ((sv >> (bsh - 1)) & 1u)) atomicOr(next_words + (dst >> 5), 1u << (dst & 31));
+                        if (next_words) {  // set or clear the bit: the word is not zeroed beforehand
+                            if ((sv >> (bsh - 1)) & 1u)
+                                atomicOr(next_words + (dst >> 5), 1u << (dst & 31));
+                            else
+                                atomicAnd(next_words + (dst >> 5), ~(1u << (dst & 31)));
+                        }
                     } else {
                         bad = true;
                     }
@@ -561,7 +563,8 @@ __device__ __forceinline__ void lw_store(const LwOut &o, const unsigned char *sp
 // starts in the copy at its destination's offset within a 32-symbol word,
 // so bitmap word k of a run is the level l + 1 bits of the k-th group of 32
 // symbols there: a word inside the run is stored, a word shared with other
-// runs is ORed into the zeroed bitmap.
+// runs (or with the padding) gets its bits by atomics that clear and set
+// only the run's own bits.
 template <typename Sym>
 __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char *split) {
     constexpr uint32_t kW = sizeof(Sym);
@@ -588,10 +591,16 @@ __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char
         const uint32_t hi = min(32u, first + len - 32 * k);
         const uint32_t mask = (hi == 32 ? ~0u : (1u << hi) - 1u) & ~((1u << lo) - 1u);
         uint32_t *w = o.next_words + ((zr ? o.gz : o.go) >> 5) + k;
-        if (mask == ~0u)
+        if (mask == ~0u) {
             *w = bits;
-        else if (bits & mask)
-            atomicOr(w, bits & mask);
+        } else {
+            // A word shared with other runs (or with the padding, zeroed by
+            // the count pass): clear this run's zero bits and set its ones;
+            // the runs' masks are disjoint, so any order of the other runs'
+            // updates leaves every bit right.
+            if (~bits & mask) atomicAnd(w, ~(~bits & mask));
+            if (bits & mask) atomicOr(w, bits & mask);
+        }
     }
 }
 

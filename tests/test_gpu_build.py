@@ -184,6 +184,38 @@ def test_async_build_on_stream_and_torch_allocator():
         W.use_torch_allocator(False)
 
 
+@pytest.mark.parametrize("matrix", [False, True])
+def test_bitmaps_exact_over_memory_full_of_ones(matrix):
+    """The passes write every bit of the level bitmaps they hand over (whole
+    words by stores, words shared by runs by clearing and setting their own
+    bits) and the padding is zeroed: built in memory that held all-ones bytes
+    (torch's caching allocator hands the library a block just filled with
+    0xFF), every level still equals the oracle's, padding included."""
+    W = wt()
+    W.use_torch_allocator(True)
+    try:
+        cases = [(96, inputs.zipf(3 * 8192 * 7 + 12345, 96, 1.0, 3), np.uint8),
+                 (4, inputs.uniform(100_003, 4, 4, np.uint8), np.uint8),
+                 (65536, inputs.zipf(200_001, 65536, 1.1, 5).astype(np.uint16), np.uint16),
+                 (1000, inputs.zipf((1 << 18) + 33, 1000, 1.0, 6).astype(np.uint16), np.uint16)]
+        for sigma, S, dtype in cases:
+            for variant in ([1] if matrix else [1, 3]):
+                junk = torch.full((64 << 20,), 255, dtype=torch.uint8, device="cuda")
+                del junk  # back to the cache, still holding the ones
+                D = to_dev(S.astype(dtype))
+                t = W.Tree.build(D, sigma, variant=variant, matrix=matrix)
+                if matrix:
+                    want = O.wm_bits(S, sigma)
+                    for l in range(want.shape[0]):
+                        assert np.array_equal(t.level(l).words.cpu().numpy().view(np.uint8), want[l]), (sigma, l)
+                else:
+                    compare_tree(t, S, sigma)
+                t.free()
+                del D
+    finally:
+        W.use_torch_allocator(False)
+
+
 @pytest.mark.parametrize("sigma,dtype,log2n,alpha,variant", [
     (96, np.uint8, 25, 1.0, 1), (4, np.uint8, 25, 0.0, 1), (96, np.uint8, 25, 1.0, 2), (4, np.uint8, 25, 0.0, 2),
     (256, np.uint8, 24, 0.0, 2), (65536, np.uint16, 23, 1.1, 1), (1 << 20, np.uint32, 22, 1.2, 1),
