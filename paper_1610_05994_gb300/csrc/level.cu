@@ -118,6 +118,25 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
         if (kFromBits) {
             constexpr uint32_t kWU = kUnitSyms / 32;  // words per unit
             const uint32_t *words = J.lv.words;
+            if (w0 + kTileWords <= nwords) {
+                // A whole tile: 16-byte loads, four lanes to a unit's 16
+                // words, the unit's count reduced by two shuffles.
+                static_assert(kWU == 16, "four lanes to a unit");
+                constexpr int kVR = (int)((kTileWords + 127) / 128);
+#pragma unroll
+                for (int r = 0; r < kVR; r++) {
+                    const uint32_t wo = (uint32_t)r * 128 + 4 * lane;  // the lane's first word in the tile
+                    uint32_t pc = 0;
+                    if (wo < kTileWords) {
+                        const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(words + w0 + wo));
+                        pc = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                    }
+                    pc += __shfl_xor_sync(0xffffffffu, pc, 1);
+                    pc += __shfl_xor_sync(0xffffffffu, pc, 2);
+                    if ((lane & 3) == 0 && wo < kTileWords) J.cnt[(size_t)tile * kU + wo / kWU] = pc;
+                }
+                continue;
+            }
             constexpr int kRows = (int)(kTileWords / 32), kSub = (int)(32 / kWU);
             const uint32_t mysub = (uint32_t)lane / kWU;
 #pragma unroll
@@ -240,45 +259,89 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
         for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
         if (lane == 0) s_base = b;
     }
-    // Four consecutive chunks per thread.
-    const uint32_t t0 = seg * kScanSeg + 4 * tid;
-    uint32_t c[4];
+    // kPer consecutive units per thread, read and written 16 bytes at a time
+    // where the segment is whole.  A unit holds at most 512 ones, so the
+    // sums of a thread, a warp and the CTA fit 32 bits.
+    constexpr int kPer = (int)(kScanSeg / 1024);
+    const uint32_t t0 = seg * kScanSeg + kPer * tid;
+    const bool whole = t0 + kPer <= nt;
+    uint32_t c[kPer];
+    if (whole) {
 #pragma unroll
-    for (int j = 0; j < 4; j++) c[j] = t0 + j < nt ? cnt[t0 + j] : 0u;
-    const uint64_t sum = (uint64_t)c[0] + c[1] + c[2] + c[3];
-    uint64_t inc = sum;
+        for (int h = 0; h < kPer / 4; h++) {
+            const uint4 v = reinterpret_cast<const uint4 *>(cnt + t0)[h];
+            c[4 * h] = v.x;
+            c[4 * h + 1] = v.y;
+            c[4 * h + 2] = v.z;
+            c[4 * h + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kPer; k++) c[k] = t0 + k < nt ? cnt[t0 + k] : 0u;
+    }
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) sum += c[k];
+    uint32_t inc = sum;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
         if (lane >= d) inc += y;
     }
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        const uint64_t w = s_warp[lane];
-        uint64_t winc = w;
+        const uint32_t w = (uint32_t)s_warp[lane];
+        uint32_t winc = w;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const uint64_t y = __shfl_up_sync(0xffffffffu, winc, d);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, winc, d);
             if (lane >= d) winc += y;
         }
         s_warp[lane] = winc - w;
     }
     __syncthreads();
-    uint64_t run = s_base + s_warp[warp] + inc - sum;
+    const uint64_t run0 = s_base + s_warp[warp] + (inc - sum);
+    uint64_t pv[kPer];  // pre[t0 + k]
+    {
+        uint64_t r = run0;
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            pv[k] = r;
+            r += c[k];
+        }
+    }
+    if (whole) {
+#pragma unroll
+        for (int h = 0; h < kPer / 2; h++)
+            reinterpret_cast<ulonglong2 *>(pre + t0)[h] = make_ulonglong2(pv[2 * h], pv[2 * h + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kPer; k++)
+            if (t0 + k < nt) pre[t0 + k] = pv[k];
+    }
     // The rank directory of level l (Section 2.2's R, Hy and select
     // samples) from the same prefixes: a rank block starts at every upb-th
     // unit; the samples of the ones (zeros) that fall in a block point to it.
     const uint32_t upb = a.upb;
+    if (way == 0) {
+        const bool vec_r = whole && upb == 1 && t0 + kPer <= J.nblocks &&
+                           (reinterpret_cast<uintptr_t>(J.lv.R + t0) & 15) == 0;
+        if (vec_r) {
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const uint32_t t = t0 + j;
-        if (t < nt) {
-            pre[t] = run;
+            for (int h = 0; h < kPer / 4; h++)
+                reinterpret_cast<uint4 *>(J.lv.R + t0)[h] =
+                    make_uint4((uint32_t)pv[4 * h], (uint32_t)pv[4 * h + 1], (uint32_t)pv[4 * h + 2],
+                               (uint32_t)pv[4 * h + 3]);
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const uint32_t t = t0 + k;
             const uint64_t b = t / upb;
-            if (way == 0 && t % upb == 0 && b < J.nblocks) {
-                const uint64_t next = run + c[j] + (upb == 2 && j + 1 < 4 ? c[j + 1] : 0u);
-                J.lv.R[b] = (uint32_t)run;
+            if (t < nt && t % upb == 0 && b < J.nblocks) {
+                const uint64_t run = pv[k];
+                const uint64_t next = run + c[k] + (upb == 2 && k + 1 < kPer ? c[k + 1] : 0u);
+                if (!vec_r) J.lv.R[b] = (uint32_t)run;
                 if ((b & kBlocksPerSpanMask) == 0) J.lv.Hy[b >> (kSpanShift - 9)] = run;
                 for (uint64_t k2 = ceil_div(run, kSample); k2 * kSample < next; k2++) J.lv.S1[k2] = (uint32_t)b;
                 const uint64_t p0 = b * 512, p1 = min(p0 + 512, J.n);
@@ -286,14 +349,14 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
                     J.lv.S0[k2] = (uint32_t)b;
             }
         }
-        run += c[j];
     }
-    if (t0 < nt && nt <= t0 + 4) {  // the total, read with the last tile's prefixes
-        pre[nt] = run;
+    if (t0 < nt && nt <= t0 + kPer) {  // the total, read with the last tile's prefixes
+        const uint64_t total = pv[kPer - 1] + c[kPer - 1];
+        pre[nt] = total;
         if (way == 0) {
-            J.lv.R[J.nblocks] = (uint32_t)run;
-            J.lv.Hy[J.nspans] = run;
-            *J.ones_out = run;
+            J.lv.R[J.nblocks] = (uint32_t)total;
+            J.lv.Hy[J.nspans] = total;
+            *J.ones_out = total;
         }
     }
 }

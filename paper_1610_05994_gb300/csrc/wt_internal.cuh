@@ -399,7 +399,7 @@ inline bool pass_writes_next_bits(uint64_t boundaries, uint64_t tiles, int width
 // (l, l + 1) = (0, 1) (way 1) and (1, 1) (way 2); the prefix scan turns each
 // into unit prefixes.  The ways live in one array each, way w at offset
 // w * stride.
-constexpr uint32_t kScanSegUnits = 4096;  // units per segment of the prefix scan
+constexpr uint32_t kScanSegUnits = 8192;  // units per segment of the prefix scan (8 per thread)
 __host__ __device__ inline uint64_t way_cnt_stride(uint64_t units) { return (units + 3) & ~3ull; }
 __host__ __device__ inline uint64_t way_pre_stride(uint64_t units) {
     return (units + 2 + ceil_div(units, kScanSegUnits) + 1 + 1) & ~1ull;
