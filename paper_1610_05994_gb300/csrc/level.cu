@@ -377,6 +377,7 @@ struct LwShared {
     LwStage st[kLwStages];
     LevelJob job;                          // the job of the claimer's latest tile
     uint64_t bar[kLwStages];               // a stage is in place
+    uint32_t lut[256];                     // zeros_first_perm of every chunk's level bits (1-byte symbols)
 };
 
 // Claims this CTA's tile g into stage s (the claiming warp, all lanes): the stage
@@ -440,6 +441,7 @@ __device__ __forceinline__ void lw_claim(const LevelLaunch &a, LwShared &sh, uns
 // split copy: for a one-node tile its two runs.
 struct LwOut {
     bool runs;               // one node: a zeros run and a ones run
+    bool bits;               // the split copy holds the runs' next-level bit streams, not their symbols
     bool store;              // the runs go out to P_{l+1} (else only their next-level bits)
     uintptr_t gz_b, go_b;    // their destinations
     uint32_t zt, ones;       // their symbols
@@ -448,6 +450,85 @@ struct LwOut {
     uint32_t *next_words;    // level l + 1's bitmap, when this pass writes it
     uint32_t bsh_next;       // level l + 1's bit
 };
+
+// The byte permutation that puts a chunk's bytes with level bit 0 first and
+// those with bit 1 after, each group in order: entry e (the chunk's 8 level
+// bits) holds two PRMT selectors, output bytes 0-3 and 4-7.
+__device__ __forceinline__ uint32_t zeros_first_perm(uint32_t e) {
+    uint32_t sel = 0;
+    int k = 0;
+    for (uint32_t want = 0; want < 2; want++)
+        for (uint32_t i = 0; i < 8; i++)
+            if (((e >> i) & 1u) == want) sel |= i << (k < 4 ? 4 * k : 16 + 4 * (k - 4)), k++;
+    return sel;
+}
+
+constexpr uint32_t kBitsOnesWord = 272;  // first word of the ones' stream in the split copy
+
+// A one-node tile of 1-byte symbols whose pass stores no order (the level
+// before the last): only level l + 1's bits of the two runs are needed, so
+// they are built as two bit streams in the split copy instead of splitting
+// the symbols.  A lane takes 32 consecutive symbols; per 8-symbol chunk a
+// byte permutation puts the chunk's zeros first, one multiply gathers the
+// permuted bytes' level l + 1 bits, and the zeros' and ones' parts are
+// appended to the lane's two bit strings; each string goes into its stream
+// at the run's offset within its first word plus the zeros (ones) of the
+// tile before the lane, by at most two shared-memory atomics.  The caller
+// copies the streams' words out with lw_next_bits.  All threads; one
+// barrier inside (after the streams are cleared).
+template <bool kWhole>
+__device__ __forceinline__ void lw_bits_tile(const uint32_t *lut, const unsigned char *buf,
+                                             const unsigned char *sbits, uint32_t *stream, uint32_t cnt,
+                                             uint32_t wx, uint32_t gz5, uint32_t go5, uint32_t Zt,
+                                             uint32_t tile_ones, uint32_t bsh_next) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nwz = Zt ? (gz5 + Zt + 31) / 32 : 0u, nwo = tile_ones ? (go5 + tile_ones + 31) / 32 : 0u;
+    for (uint32_t t = tid; t < nwz; t += kLwThreads) stream[t] = 0u;
+    for (uint32_t t = tid; t < nwo; t += kLwThreads) stream[kBitsOnesWord + t] = 0u;
+    __syncthreads();
+    const BitGather gg = bit_gather<uint8_t>(bsh_next);
+    uint32_t oc = wx;  // ones of the tile before the warp's round
+#pragma unroll
+    for (uint32_t r = 0; r < kLwWarpBytes / 1024; r++) {
+        const uint32_t p0 = warp * kLwWarpBytes + r * 1024 + 32 * lane;  // the lane's first symbol
+        uint32_t vm = ~0u;                                                  // its symbols below cnt
+        if (!kWhole) vm = p0 >= cnt ? 0u : (cnt - p0 >= 32 ? ~0u : (1u << (cnt - p0)) - 1u);
+        const uint32_t hb = vm ? reinterpret_cast<const uint32_t *>(sbits)[p0 / 32] & vm : 0u;
+        uint32_t tot;
+        const uint32_t po = oc + warp_excl_scan((uint32_t)__popc(hb), lane, tot);  // ones of the tile before p0
+        oc += tot;
+        if (!vm) continue;
+        const uint4 v0 = *reinterpret_cast<const uint4 *>(buf + p0);
+        const uint4 v1 = *reinterpret_cast<const uint4 *>(buf + p0 + 16);
+        const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint32_t zacc = 0, oacc = 0, zs = 0, os = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t h8 = (hb >> (8 * j)) & 0xffu;
+            const uint32_t sel = lut[h8];
+            const uint64_t X = ((uint64_t)__byte_perm(w[2 * j], w[2 * j + 1], sel >> 16) << 32) |
+                               __byte_perm(w[2 * j], w[2 * j + 1], sel & 0xffffu);
+            const uint32_t g = (uint32_t)(((X & gg.mask) * gg.mul) >> 56);  // next bits, zeros first
+            const uint32_t o8 = (uint32_t)__popc(h8);
+            const uint32_t zv = (uint32_t)__popc(~h8 & (vm >> (8 * j)) & 0xffu);  // the chunk's zeros below cnt
+            zacc |= (g & ((1u << zv) - 1u)) << zs;
+            zs += zv;
+            oacc |= (g >> (8 - o8)) << os;
+            os += o8;
+        }
+        const uint32_t zoff = gz5 + (p0 - po), ooff = go5 + po;  // the strings' first bits in the streams
+        if (zacc) {
+            const uint32_t wi = zoff >> 5, sh = zoff & 31;
+            atomicOr(stream + wi, zacc << sh);
+            if (sh && sh + zs > 32) atomicOr(stream + wi + 1, zacc >> (32 - sh));
+        }
+        if (oacc) {
+            const uint32_t wi = kBitsOnesWord + (ooff >> 5), sh = ooff & 31;
+            atomicOr(stream + wi, oacc << sh);
+            if (sh && sh + os > 32) atomicOr(stream + wi + 1, oacc >> (32 - sh));
+        }
+    }
+}
 
 // One tile: count and placement into the split copy, which the caller sends
 // out with lw_store after its next barrier (all threads).  Each warp works
@@ -458,8 +539,9 @@ struct LwOut {
 // barrier, from the split copy), multi-node tiles bit by bit here.
 // kWhole: the tile holds kTile symbols (no bound checks per symbol).
 template <typename Sym, bool kWhole>
-__device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, const unsigned char *buf,
-                                        const unsigned char *sbits, unsigned char *split, bool &bad, LwOut &out) {
+__device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, const uint32_t *lut,
+                                        const unsigned char *buf, const unsigned char *sbits, unsigned char *split,
+                                        bool &bad, LwOut &out) {
     using Cfg = LwCfg<Sym>;
     constexpr int kW = Cfg::kW;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -474,6 +556,36 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     const uint32_t Zt = cnt - tile_ones;
     const uint32_t bsh = J.L - 1 - l;     // the level-l bit
     uint32_t *const next_words = J.next_words;
+    const uint32_t shv = J.L - l;  // key_l = s >> shv
+    const uint32_t nodes = 1u << l;
+    const Sym *sb = reinterpret_cast<const Sym *>(buf);
+    const uint32_t kfirst = a.one_node ? 0u : (uint32_t)sb[0] >> shv;
+    const uint32_t klast = a.one_node ? 0u : (uint32_t)sb[cnt - 1] >> shv;
+    Sym *nxt = static_cast<Sym *>(J.nxt);
+    out.bits = false;
+    if (kW == 1 && nxt == nullptr && next_words != nullptr && kfirst == klast && kfirst < nodes) {
+        // The level before the last, a one-node tile: only level l + 1's
+        // bits of its two runs are needed (lw_bits_tile).
+        const uint64_t gz = (base - P) + __ldg(J.ob + kfirst), go = P + __ldg(J.ze + kfirst);
+        const bool ok = gz + Zt <= J.n && go + tile_ones <= J.n;  // the same in every thread
+        if (ok)
+            lw_bits_tile<kWhole>(lut, buf, sbits, reinterpret_cast<uint32_t *>(split), cnt, wx,
+                                 (uint32_t)(gz & 31), (uint32_t)(go & 31), Zt, tile_ones, bsh - 1);
+        else
+            bad = true;
+        out.runs = ok;
+        out.bits = ok;
+        out.store = false;
+        out.gz_b = out.go_b = 0;
+        out.zt = Zt;
+        out.ones = tile_ones;
+        out.offz = out.B1 = 0;
+        out.gz = gz;
+        out.go = go;
+        out.next_words = next_words;
+        out.bsh_next = bsh - 1;
+        return;
+    }
 
     // Count: level bits of the lane's chunks, per-lane and per-warp ones.  A
     // lane takes 8 consecutive bytes of each 256-byte warp step (8, 4 or 2
@@ -505,12 +617,6 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     uintptr_t gz_b = 0, go_b = 0;
     uint32_t offz = 0, B1 = 0;
     uint64_t gz = 0, go = 0;
-    const uint32_t shv = J.L - l;  // key_l = s >> shv
-    const uint32_t nodes = 1u << l;
-    const Sym *sb = reinterpret_cast<const Sym *>(buf);
-    const uint32_t kfirst = a.one_node ? 0u : (uint32_t)sb[0] >> shv;
-    const uint32_t klast = a.one_node ? 0u : (uint32_t)sb[cnt - 1] >> shv;
-    Sym *nxt = static_cast<Sym *>(J.nxt);
     if (kfirst == klast && kfirst < nodes) {
         gz = (base - P) + __ldg(J.ob + kfirst);  // first zero's position in P_{l+1}
         go = P + __ldg(J.ze + kfirst);           // first one's position
@@ -640,13 +746,17 @@ __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char
     for (uint32_t t = threadIdx.x; t < nwz + nwo; t += kLwThreads) {
         const bool zr = t < nwz;
         const uint32_t k = zr ? t : t - nwz;
-        const unsigned char *g = split + (zr ? zbase : obase) + k * kGroup;
         uint32_t bits = 0;
+        if (o.bits) {  // the run's word k of its bit stream
+            bits = reinterpret_cast<const uint32_t *>(split)[(zr ? 0u : kBitsOnesWord) + k];
+        } else {
+            const unsigned char *g = split + (zr ? zbase : obase) + k * kGroup;
 #pragma unroll
-        for (uint32_t c = 0; c < kW * 2; c++) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(g + 16 * c);
-            const uint32_t x[4] = {v.x, v.y, v.z, v.w};
-            bits |= gather_bits<Sym>(x, gg, o.bsh_next) << (c * (16 / kW));
+            for (uint32_t c = 0; c < kW * 2; c++) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(g + 16 * c);
+                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+                bits |= gather_bits<Sym>(x, gg, o.bsh_next) << (c * (16 / kW));
+            }
         }
         const uint32_t first = (uint32_t)((zr ? o.gz : o.go) & 31);   // the run's first bit in word 0
         const uint32_t len = zr ? o.zt : o.ones;
@@ -689,6 +799,8 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
         for (int s = 0; s < kLwStages; s++) mbar_init(&sh.bar[s], 1);
         fence_mbar_init();
     }
+    if (sizeof(Sym) == 1)
+        for (uint32_t e = tid; e < 256; e += kLwThreads) sh.lut[e] = zeros_first_perm(e);
     __syncthreads();
     if (claimer) {
         if (g_begin < g_end) k = find_job(a, g_begin);
@@ -714,6 +826,7 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
         unsigned char *split = split_base + par * kLwSplitBytes;
         LwOut out;
         out.runs = false;
+        out.bits = false;
         if (!S.skip) {
             const LevelJob &J = S.J;
             const uint32_t tile = S.tile;
@@ -729,9 +842,9 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
             }
             const unsigned char *sbits = in + kLwStages * kLwTileBytes + s * kLwStageBits;
             if (cnt == Cfg::kTile)
-                lw_tile<Sym, true>(a, S, buf, sbits, split, bad, out);
+                lw_tile<Sym, true>(a, S, sh.lut, buf, sbits, split, bad, out);
             else
-                lw_tile<Sym, false>(a, S, buf, sbits, split, bad, out);
+                lw_tile<Sym, false>(a, S, sh.lut, buf, sbits, split, bad, out);
         }
         // The split copy of the other parity (tile i - 1) is reused by tile
         // i + 1: its bulk stores must have read it before the barrier (its
