@@ -897,6 +897,7 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         bool from_bits;           // level l's bitmaps were written by the passes of level l - 1
         bool next_bits;           // this level's pass writes level l + 1's bitmaps
         bool do_pass;             // some sequence has a level l + 1
+        bool bits;                // some sequence stores no order (the level before its last, bitmap handed over)
     };
     std::vector<LaunchPlan> plans;
     for (int c = 0; c < 3; c++)
@@ -1028,12 +1029,16 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
         P.next_bits = P.do_pass && pass_writes_next_bits(bnd, ptiles, P.width);
         P.from_bits = P.l > 0 && prev_next_bits[wclass(P.width)];
         prev_next_bits[wclass(P.width)] = P.next_bits;
+        P.bits = false;
         for (size_t q = 0; q < P.seqs.size(); q++) {
             const uint32_t k = P.seqs[q];
             const uint32_t l = P.l;
             const uint64_t ntk = ceil_div(n[k], lw_tile_elems(width[k]));
             const void *cur = l == 0 ? S[k] : sc + ((l & 1) ? so[k].ping : so[k].pong);
-            void *nxt = sc + ((l & 1) ? so[k].pong : so[k].ping);
+            // The last level needs no symbols when its bitmap is handed over.
+            const bool no_order = P.next_bits && L[k] == l + 2;
+            P.bits = P.bits || no_order;
+            void *nxt = no_order ? nullptr : sc + ((l & 1) ? so[k].pong : so[k].ping);
             pj[q] = make_level_job(cur, nxt, n[k], width[k], L[k], l, reinterpret_cast<uint64_t *>(sc + so[k].ob),
                                    reinterpret_cast<uint64_t *>(sc + so[k].ze), hdesc[k].lv[l],
                                    &d_descs[k].lv[l].ones, reinterpret_cast<uint32_t *>(sc + so[k].cnt),
@@ -1094,7 +1099,8 @@ wt_status build_batch_impl(const void *const *S, const uint64_t *n, const uint64
             ProfScope p(K_LEVEL_PASS, bytes, st);
             ck(launch_level_jobs(P.width, P.l, reinterpret_cast<const LevelJob *>(dt + P.jobs_off),
                                  reinterpret_cast<const uint32_t *>(dt + P.ts_off), (uint32_t)P.seqs.size(), P.total,
-                                 P.max_tiles, P.from_bits, P.do_pass, B->d_err, st));
+                                 P.max_tiles, P.from_bits, P.do_pass, B->d_err, st, false, nullptr, 0, false,
+                                 P.bits));
         }
     }
     if (use_graph) {

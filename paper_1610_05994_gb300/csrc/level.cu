@@ -538,7 +538,8 @@ __device__ __forceinline__ void lw_bits_tile(const uint32_t *lut, const unsigned
 // l + 1's: one-node tiles through lw_next_bits (the caller, after its
 // barrier, from the split copy), multi-node tiles bit by bit here.
 // kWhole: the tile holds kTile symbols (no bound checks per symbol).
-template <typename Sym, bool kWhole>
+// kBits: the launch has jobs on the level before the last (lw_bits_tile).
+template <typename Sym, bool kWhole, bool kBits>
 __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, const uint32_t *lut,
                                         const unsigned char *buf, const unsigned char *sbits, unsigned char *split,
                                         bool &bad, LwOut &out) {
@@ -563,7 +564,7 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
     const uint32_t klast = a.one_node ? 0u : (uint32_t)sb[cnt - 1] >> shv;
     Sym *nxt = static_cast<Sym *>(J.nxt);
     out.bits = false;
-    if (kW == 1 && nxt == nullptr && next_words != nullptr && kfirst == klast && kfirst < nodes) {
+    if (kBits && kW == 1 && nxt == nullptr && next_words != nullptr && kfirst == klast && kfirst < nodes) {
         // The level before the last, a one-node tile: only level l + 1's
         // bits of its two runs are needed (lw_bits_tile).
         const uint64_t gz = (base - P) + __ldg(J.ob + kfirst), go = P + __ldg(J.ze + kfirst);
@@ -734,7 +735,7 @@ __device__ __forceinline__ void lw_store(const LwOut &o, const unsigned char *sp
 // symbols there: a word inside the run is stored, a word shared with other
 // runs (or with the padding) gets its bits by atomics that clear and set
 // only the run's own bits.
-template <typename Sym>
+template <typename Sym, bool kBits>
 __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char *split) {
     constexpr uint32_t kW = sizeof(Sym);
     constexpr uint32_t kGroup = 32 * kW;  // bytes of 32 symbols
@@ -747,7 +748,7 @@ __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char
         const bool zr = t < nwz;
         const uint32_t k = zr ? t : t - nwz;
         uint32_t bits = 0;
-        if (o.bits) {  // the run's word k of its bit stream
+        if (kBits && o.bits) {  // the run's word k of its bit stream
             bits = reinterpret_cast<const uint32_t *>(split)[(zr ? 0u : kBitsOnesWord) + k];
         } else {
             const unsigned char *g = split + (zr ? zbase : obase) + k * kGroup;
@@ -777,7 +778,7 @@ __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char
     }
 }
 
-template <typename Sym>
+template <typename Sym, bool kBits>
 __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_kernel(LevelLaunch a) {
     using Cfg = LwCfg<Sym>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -799,7 +800,7 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
         for (int s = 0; s < kLwStages; s++) mbar_init(&sh.bar[s], 1);
         fence_mbar_init();
     }
-    if (sizeof(Sym) == 1)
+    if (kBits && sizeof(Sym) == 1)
         for (uint32_t e = tid; e < 256; e += kLwThreads) sh.lut[e] = zeros_first_perm(e);
     __syncthreads();
     if (claimer) {
@@ -842,9 +843,9 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
             }
             const unsigned char *sbits = in + kLwStages * kLwTileBytes + s * kLwStageBits;
             if (cnt == Cfg::kTile)
-                lw_tile<Sym, true>(a, S, sh.lut, buf, sbits, split, bad, out);
+                lw_tile<Sym, true, kBits>(a, S, sh.lut, buf, sbits, split, bad, out);
             else
-                lw_tile<Sym, false>(a, S, sh.lut, buf, sbits, split, bad, out);
+                lw_tile<Sym, false, kBits>(a, S, sh.lut, buf, sbits, split, bad, out);
         }
         // The split copy of the other parity (tile i - 1) is reused by tile
         // i + 1: its bulk stores must have read it before the barrier (its
@@ -858,7 +859,7 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
         }
         lw_store<Sym>(out, split);
         if (tid == 0 || tid == 32) bulk_commit();
-        lw_next_bits<Sym>(out, split);
+        lw_next_bits<Sym, kBits>(out, split);
     }
     if (tid == 0 || tid == 32) bulk_wait_all();
     if (failed && tid == 0) atomicOr(a.err, kErrTimeout);
@@ -869,27 +870,37 @@ constexpr size_t kLwSmem = kLwStages * (kLwTileBytes + kLwStageBits) + 2 * kLwSp
 // Six CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA.
 static_assert(LwCfg<uint8_t>::kMinCtas * (kLwSmem + 1024) <= 228 * 1024, "level pass shared memory");
 
-template <typename Sym>
-static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass, bool counted, cudaStream_t st,
-                             const RankTables *rt) {
-    // Persistent grid: every resident CTA slot, at most one CTA per tile.
-    static int slots = 0, sms = 0;
+// Resident CTA slots of level_pass_kernel<Sym, kBits> (set up once).
+template <typename Sym, bool kBits>
+static int lw_slots(int &sms) {
+    static int slots = 0, count = 0;
     if (!slots) {
-        cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<Sym>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kLwSmem);
-        if (e != cudaSuccess) return e;
+        if (cudaFuncSetAttribute(level_pass_kernel<Sym, kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kLwSmem) != cudaSuccess)
+            return 0;
         int dev = 0, per_sm = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_pass_kernel<Sym>, kLwThreads, kLwSmem) !=
-                cudaSuccess ||
+        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+        if (count <= 0) count = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_pass_kernel<Sym, kBits>, kLwThreads,
+                                                          kLwSmem) != cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
         }
-        slots = sms * per_sm;
+        slots = count * per_sm;
     }
+    sms = count;
+    return slots;
+}
+
+template <typename Sym>
+static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass, bool counted, cudaStream_t st,
+                             const RankTables *rt, bool bits) {
+    // Persistent grid: every resident CTA slot, at most one CTA per tile.
+    int sms = 0;
+    const int slots = bits ? lw_slots<Sym, true>(sms) : lw_slots<Sym, false>(sms);
+    if (!slots) return cudaErrorInvalidValue;
     // Counts: a warp per tile, at most eight CTAs per SM.
     const uint32_t cw = (a.total_tiles + kCountWarps - 1) / kCountWarps;
     const uint32_t g0 = cw < (uint32_t)(sms * 8) ? cw : (uint32_t)(sms * 8);
@@ -910,7 +921,10 @@ static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass,
     }
     if (do_pass) {
         const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
-        level_pass_kernel<Sym><<<grid, kLwThreads, kLwSmem, st>>>(a);
+        if (bits)
+            level_pass_kernel<Sym, true><<<grid, kLwThreads, kLwSmem, st>>>(a);
+        else
+            level_pass_kernel<Sym, false><<<grid, kLwThreads, kLwSmem, st>>>(a);
         note_launches(1);
     }
     return cudaGetLastError();
@@ -940,7 +954,7 @@ LevelJob make_level_job(const void *cur, void *nxt, uint64_t n, int width, uint3
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
                               uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
                               uint32_t *err, cudaStream_t st, bool counted, const RankTables *rt,
-                              uint32_t check_sigma, bool one_node) {
+                              uint32_t check_sigma, bool one_node, bool bits) {
     if (njobs == 0 || total_tiles == 0) return cudaSuccess;
     LevelLaunch a{};
     a.jobs = jobs;
@@ -956,9 +970,9 @@ cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const
     a.check_sigma = check_sigma;
     a.one_node = one_node;
     switch (width) {
-        case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, counted, st, rt);
-        case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, counted, st, rt);
-        case 4: return launch_lw<uint32_t>(a, from_bits, do_pass, counted, st, rt);
+        case 1: return launch_lw<uint8_t>(a, from_bits, do_pass, counted, st, rt, bits);
+        case 2: return launch_lw<uint16_t>(a, from_bits, do_pass, counted, st, rt, false);
+        case 4: return launch_lw<uint32_t>(a, from_bits, do_pass, counted, st, rt, false);
     }
     return cudaErrorInvalidValue;
 }
@@ -1057,7 +1071,7 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, from_bits, l + 1 < L, err, st, counted, rt,
-                             check_sigma, one_node);
+                             check_sigma, one_node, j.nxt == nullptr && j.next_words != nullptr);
 }
 
 }  // namespace wt

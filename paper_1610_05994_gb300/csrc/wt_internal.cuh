@@ -462,7 +462,9 @@ struct RankTables {
 cudaError_t launch_level_jobs(int width, uint32_t l, const LevelJob *jobs, const uint32_t *tile_start, uint32_t njobs,
                               uint32_t total_tiles, uint32_t max_job_tiles, bool from_bits, bool do_pass,
                               uint32_t *err, cudaStream_t st, bool counted = false, const RankTables *rt = nullptr,
-                              uint32_t check_sigma = 0, bool one_node = false);
+                              uint32_t check_sigma = 0, bool one_node = false, bool bits = false);
+// bits: some job of the launch stores no order (the level before its last)
+// while handing over the next bitmap (1-byte codes take lw_bits_tile).
 // One sequence (job_slot: level_job_slot_bytes() of device memory).
 // one_node: every node of level l has the same offsets (the wavelet
 // matrix), so every tile is placed as one node whatever its keys.
