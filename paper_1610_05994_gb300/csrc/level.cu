@@ -36,12 +36,15 @@
 //     counts of three steps share one shuffle scan;
 //   * when the whole tile lies in one node (the common case: nodes are far
 //     larger than a tile except on the deepest levels of large alphabets),
-//     its zeros and ones go to two contiguous runs of P_{l+1}: each lane
-//     walks its symbols in order with one running pointer, writing every
-//     symbol into a shared-memory split copy of the two runs laid out at the
-//     destination's offset within a 32-symbol bitmap word (which also agrees
-//     with the destination modulo 16 bytes); the aligned interior of each
-//     run leaves with one bulk store, the ragged ends with byte stores.
+//     its zeros and ones go to two contiguous runs of P_{l+1}: every symbol
+//     is written into a shared-memory split copy of the two runs laid out at
+//     the destination's offset within a 32-symbol bitmap word (which also
+//     agrees with the destination modulo 16 bytes); for whole tiles of
+//     1-byte symbols one byte permutation per 8-byte chunk puts its zeros
+//     first and its ones after, so each byte's place is the chunk's first
+//     zero or first one plus a constant; otherwise each lane walks its
+//     symbols with one running pointer.  The aligned interior of each run
+//     leaves with one bulk store, the ragged ends with byte stores.
 //     Tiles that span several nodes store every symbol at its own
 //     destination.
 //   * one CTA barrier per tile: it hands the split copy to the threads that
@@ -640,6 +643,23 @@ __device__ __forceinline__ void lw_tile(const LevelLaunch &a, const LwStage &S, 
                 const uint32_t o = wx + stx + ((lpk[st / 3] >> sh10) & 0x3ffu);  // ones before the chunk
                 stx += (tpk[st / 3] >> sh10) & 0x3ffu;
                 const uint2 v = *reinterpret_cast<const uint2 *>(buf + q);
+                if (kW == 1 && kWhole) {
+                    // Bytes: one byte permutation puts the chunk's zeros
+                    // first and its ones after, each group in order, so
+                    // permuted byte j goes to the chunk's first zero + j
+                    // (j < z) or to its first one + (j - z).
+                    const uint32_t h8 = h[st];
+                    const uint32_t z = 8u - (uint32_t)__popc(h8);
+                    const uint32_t sel = lut[h8];
+                    const uint32_t xl = __byte_perm(v.x, v.y, sel & 0xffffu);
+                    const uint32_t xh = __byte_perm(v.x, v.y, sel >> 16);
+                    const uint32_t zp = offz + q - o;  // the chunk's first zero (zeros of the tile before it)
+                    const uint32_t opz = B1 + o - z;   // its first one, less z
+#pragma unroll
+                    for (uint32_t j = 0; j < 8; j++)
+                        split[(j < z ? zp : opz) + j] = (unsigned char)((j < 4 ? xl : xh) >> (8 * (j & 3)));
+                    continue;
+                }
                 const uint32_t x[4] = {v.x, v.y, 0u, 0u};
                 // A one goes to po; a zero to C + k kW - po (its zeros-before, scaled).
                 uint32_t po = B1 + o * kW;
@@ -800,7 +820,7 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
         for (int s = 0; s < kLwStages; s++) mbar_init(&sh.bar[s], 1);
         fence_mbar_init();
     }
-    if (kBits && sizeof(Sym) == 1)
+    if (sizeof(Sym) == 1)
         for (uint32_t e = tid; e < 256; e += kLwThreads) sh.lut[e] = zeros_first_perm(e);
     __syncthreads();
     if (claimer) {
