@@ -754,24 +754,30 @@ __device__ __forceinline__ void lw_store(const LwOut &o, const unsigned char *sp
 // so bitmap word k of a run is the level l + 1 bits of the k-th group of 32
 // symbols there: a word inside the run is stored, a word shared with other
 // runs (or with the padding) gets its bits by atomics that clear and set
-// only the run's own bits.
+// only the run's own bits.  The two runs have 256 to 258 words; thread
+// (tid + 64) mod 128 takes words t, t + 128, ..., so the at most two words
+// beyond 256 fall to warp 2, which neither claims stages nor issues the
+// bulk stores.
 template <typename Sym, bool kBits>
 __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char *split) {
     constexpr uint32_t kW = sizeof(Sym);
     constexpr uint32_t kGroup = 32 * kW;  // bytes of 32 symbols
     if (!o.runs || !o.next_words) return;
-    const uint32_t nwz = o.zt ? ((uint32_t)(o.gz & 31) + o.zt + 31) / 32 : 0u;
-    const uint32_t nwo = o.ones ? ((uint32_t)(o.go & 31) + o.ones + 31) / 32 : 0u;
-    const uint32_t zbase = 0, obase = o.B1 - (uint32_t)(o.go & 31) * kW;  // group 0 of each run
+    const uint32_t fz = (uint32_t)(o.gz & 31), fo = (uint32_t)(o.go & 31);  // each run's first bit in its word 0
+    const uint32_t ez = fz + o.zt, eo = fo + o.ones;                         // and its end, from word 0's first bit
+    const uint32_t nwz = o.zt ? (ez + 31) / 32 : 0u;
+    const uint32_t nw = nwz + (o.ones ? (eo + 31) / 32 : 0u);
+    const uint32_t obase = o.B1 - fo * kW;  // group 0 of the ones' run in the copy
+    uint32_t *const zw = o.next_words + (o.gz >> 5), *const ow = o.next_words + (o.go >> 5);
     const BitGather gg = bit_gather<Sym>(o.bsh_next);
-    for (uint32_t t = threadIdx.x; t < nwz + nwo; t += kLwThreads) {
+    for (uint32_t t = (threadIdx.x + 64) & (kLwThreads - 1); t < nw; t += kLwThreads) {
         const bool zr = t < nwz;
         const uint32_t k = zr ? t : t - nwz;
         uint32_t bits = 0;
         if (kBits && o.bits) {  // the run's word k of its bit stream
             bits = reinterpret_cast<const uint32_t *>(split)[(zr ? 0u : kBitsOnesWord) + k];
         } else {
-            const unsigned char *g = split + (zr ? zbase : obase) + k * kGroup;
+            const unsigned char *g = split + (zr ? 0u : obase) + k * kGroup;
 #pragma unroll
             for (uint32_t c = 0; c < kW * 2; c++) {
                 const uint4 v = *reinterpret_cast<const uint4 *>(g + 16 * c);
@@ -779,19 +785,17 @@ __device__ __forceinline__ void lw_next_bits(const LwOut &o, const unsigned char
                 bits |= gather_bits<Sym>(x, gg, o.bsh_next) << (c * (16 / kW));
             }
         }
-        const uint32_t first = (uint32_t)((zr ? o.gz : o.go) & 31);   // the run's first bit in word 0
-        const uint32_t len = zr ? o.zt : o.ones;
-        const uint32_t lo = k == 0 ? first : 0u;                      // bits of the run in word k
-        const uint32_t hi = min(32u, first + len - 32 * k);
-        const uint32_t mask = (hi == 32 ? ~0u : (1u << hi) - 1u) & ~((1u << lo) - 1u);
-        uint32_t *w = o.next_words + ((zr ? o.gz : o.go) >> 5) + k;
-        if (mask == ~0u) {
-            *w = bits;
+        uint32_t *w = (zr ? zw : ow) + k;
+        const uint32_t first = zr ? fz : fo, end = zr ? ez : eo;
+        if ((k > 0 || first == 0) && 32 * k + 32 <= end) {
+            *w = bits;  // inside the run
         } else {
             // A word shared with other runs (or with the padding, zeroed by
-            // the count pass): clear this run's zero bits and set its ones;
-            // the runs' masks are disjoint, so any order of the other runs'
+            // the scan): clear this run's zero bits and set its ones; the
+            // runs' masks are disjoint, so any order of the other runs'
             // updates leaves every bit right.
+            const uint32_t lo = k == 0 ? first : 0u, hi = min(32u, end - 32 * k);
+            const uint32_t mask = (hi == 32 ? ~0u : (1u << hi) - 1u) & ~((1u << lo) - 1u);
             if (~bits & mask) atomicAnd(w, ~(~bits & mask));
             if (bits & mask) atomicOr(w, bits & mask);
         }
