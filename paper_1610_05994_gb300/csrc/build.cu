@@ -614,6 +614,7 @@ __global__ void __launch_bounds__(256) rank_tables_kernel(LevelDesc lv, uint64_t
                                                           const uint64_t *__restrict__ start_in,
                                                           uint64_t *__restrict__ ob, uint64_t *__restrict__ ze,
                                                           uint64_t *__restrict__ start_out) {
+    griddep_wait();
     const uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (v >= nodes) return;
     const uint64_t c0 = start_in[v], c1 = start_in[v + 1];
@@ -641,9 +642,10 @@ cudaError_t launch_root_starts(uint64_t n, uint64_t *start, cudaStream_t st) {
 cudaError_t launch_rank_tables(const LevelDesc &lv, uint32_t l, const uint64_t *start_in, uint64_t *ob,
                                uint64_t *ze, uint64_t *start_out, cudaStream_t st) {
     const uint64_t nodes = 1ull << l;
-    rank_tables_kernel<<<(unsigned)ceil_div(nodes, 256), 256, 0, st>>>(lv, nodes, start_in, ob, ze, start_out);
+    const cudaError_t e = launch_dependent(rank_tables_kernel, (unsigned)ceil_div(nodes, 256), 256, 0, st, lv, nodes,
+                                           start_in, ob, ze, start_out);
     note_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace wt

@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
     constexpr uint32_t kU = Cfg::kUnits;
     constexpr uint32_t kUnitSyms = Cfg::kTile / kU;
     constexpr uint32_t kTileWords = Cfg::kTile / 32;  // bitmap words of a tile
+    griddep_wait();
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kCountWarps;
     const uint32_t bsh_l = 1 + a.l;
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(LevelLaunch a) 
 // (the level-l ones) writes the directory.
 __global__ void __launch_bounds__(1024) scan_sums_kernel(LevelLaunch a) {
     __shared__ uint32_t part[32];
+    griddep_wait();
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
     const LevelJob &J = a.jobs[job];
     const uint32_t nt = J.ntiles * a.units;  // units
@@ -242,6 +244,7 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(LevelLaunch a) {
 __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     __shared__ uint64_t s_warp[32];
     __shared__ uint64_t s_base;
+    griddep_wait();
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
     const LevelJob &J = a.jobs[job];
     const uint32_t nt = J.ntiles * a.units;  // units
@@ -827,6 +830,8 @@ __global__ void __launch_bounds__(kLwThreads, LwCfg<Sym>::kMinCtas) level_pass_k
     if (sizeof(Sym) == 1)
         for (uint32_t e = tid; e < 256; e += kLwThreads) sh.lut[e] = zeros_first_perm(e);
     __syncthreads();
+    // The set-up above touches only this CTA's shared memory.
+    griddep_wait();
     if (claimer) {
         if (g_begin < g_end) k = find_job(a, g_begin);
         for (int s = 0; s < kLwStages - 1; s++) lw_claim<Sym>(a, sh, in, s, g_begin + s, g_end, k, have_job);
@@ -929,27 +934,26 @@ static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass,
     const uint32_t cw = (a.total_tiles + kCountWarps - 1) / kCountWarps;
     const uint32_t g0 = cw < (uint32_t)(sms * 8) ? cw : (uint32_t)(sms * 8);
     if (!counted) {
-        if (from_bits)
-            count_kernel<Sym, true><<<g0, kCountThreads, 0, st>>>(a);
-        else
-            count_kernel<Sym, false><<<g0, kCountThreads, 0, st>>>(a);
+        const cudaError_t e = from_bits ? launch_dependent(count_kernel<Sym, true>, g0, kCountThreads, 0, st, a)
+                                        : launch_dependent(count_kernel<Sym, false>, g0, kCountThreads, 0, st, a);
         note_launches(1);
+        if (e != cudaSuccess) return e;
     }
     const dim3 sg(a.njobs * a.segs, a.ways);
-    scan_sums_kernel<<<sg, 1024, 0, st>>>(a);
-    scan_segs_kernel<<<sg, 1024, 0, st>>>(a);
+    cudaError_t e = launch_dependent(scan_sums_kernel, sg, 1024, 0, st, a);
+    if (e == cudaSuccess) e = launch_dependent(scan_segs_kernel, sg, 1024, 0, st, a);
     note_launches(2);
+    if (e != cudaSuccess) return e;
     if (rt) {  // the level's node tables from its directory (no histogram)
         const cudaError_t e = launch_rank_tables(rt->lv, a.l, rt->start_in, rt->ob, rt->ze, rt->start_out, st);
         if (e != cudaSuccess) return e;
     }
     if (do_pass) {
         const int grid = (int)(a.total_tiles < (uint32_t)slots ? a.total_tiles : (uint32_t)slots);
-        if (bits)
-            level_pass_kernel<Sym, true><<<grid, kLwThreads, kLwSmem, st>>>(a);
-        else
-            level_pass_kernel<Sym, false><<<grid, kLwThreads, kLwSmem, st>>>(a);
+        e = bits ? launch_dependent(level_pass_kernel<Sym, true>, grid, kLwThreads, kLwSmem, st, a)
+                 : launch_dependent(level_pass_kernel<Sym, false>, grid, kLwThreads, kLwSmem, st, a);
         note_launches(1);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -1021,6 +1025,7 @@ cudaError_t launch_level_scans(int width, uint32_t l, const LevelJob *jobs, uint
 // Writes one job and its tile range to device memory (kernel parameters
 // carry the values, so no host buffer has to outlive the call).
 __global__ void put_job_kernel(LevelJob j, LevelJob *dst, uint32_t *tile_start) {
+    griddep_wait();  // the slot may still be read by the previous level's kernels
     *dst = j;
     tile_start[0] = 0;
     tile_start[1] = j.ntiles;
@@ -1038,8 +1043,9 @@ cudaError_t launch_level_count(const void *cur, uint64_t n, int width, uint32_t 
                                 next_words);
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
     uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
-    put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
+    const cudaError_t pe = launch_dependent(put_job_kernel, 1, 1, 0, st, j, dj, ts);
     note_launches(1);
+    if (pe != cudaSuccess) return pe;
     LevelLaunch a{};
     a.jobs = dj;
     a.tile_start = ts;
@@ -1057,14 +1063,15 @@ cudaError_t launch_level_count(const void *cur, uint64_t n, int width, uint32_t 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint32_t g0 = cw < (uint32_t)(sms * 8) ? cw : (uint32_t)(sms * 8);
+    cudaError_t e = cudaErrorInvalidValue;
     switch (width) {
-        case 1: count_kernel<uint8_t, false><<<g0, kCountThreads, 0, st>>>(a); break;
-        case 2: count_kernel<uint16_t, false><<<g0, kCountThreads, 0, st>>>(a); break;
-        case 4: count_kernel<uint32_t, false><<<g0, kCountThreads, 0, st>>>(a); break;
+        case 1: e = launch_dependent(count_kernel<uint8_t, false>, g0, kCountThreads, 0, st, a); break;
+        case 2: e = launch_dependent(count_kernel<uint16_t, false>, g0, kCountThreads, 0, st, a); break;
+        case 4: e = launch_dependent(count_kernel<uint32_t, false>, g0, kCountThreads, 0, st, a); break;
         default: return cudaErrorInvalidValue;
     }
     note_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_level_directory(uint64_t n, int width, uint32_t L, uint32_t l, LevelDesc lv, uint64_t *ones_out,
@@ -1074,8 +1081,9 @@ cudaError_t launch_level_directory(uint64_t n, int width, uint32_t L, uint32_t l
     j.nxt = nullptr;
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
     uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
-    put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
+    const cudaError_t pe = launch_dependent(put_job_kernel, 1, 1, 0, st, j, dj, ts);
     note_launches(1);
+    if (pe != cudaSuccess) return pe;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, true, false, err, st, false);
@@ -1090,8 +1098,9 @@ cudaError_t launch_level_pass(const void *cur, void *nxt, uint64_t n, int width,
     const LevelJob j = make_level_job(cur, nxt, n, width, L, l, ob, ze, lv, ones_out, cnt, pre, next_words);
     LevelJob *dj = static_cast<LevelJob *>(job_slot);
     uint32_t *ts = reinterpret_cast<uint32_t *>(dj + 1);
-    put_job_kernel<<<1, 1, 0, st>>>(j, dj, ts);
+    const cudaError_t pe = launch_dependent(put_job_kernel, 1, 1, 0, st, j, dj, ts);
     note_launches(1);
+    if (pe != cudaSuccess) return pe;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_level_jobs(width, l, dj, ts, 1, j.ntiles, j.ntiles, from_bits, l + 1 < L, err, st, counted, rt,
