@@ -371,12 +371,15 @@ wt_status wt_wait_selftest(uint64_t limit_ns, int arrive, uint32_t *err_word, vo
 
 /*
  * Per-kernel timing (no counterpart in the paper; it times the hot path).
- * Between wt_profile_begin and wt_profile_end every kernel launch of the
- * library is bracketed by CUDA events on the stream it runs on.
+ * Between wt_profile_begin and wt_profile_end the library's kernel
+ * launches are bracketed by CUDA events on the stream they run on.
  * wt_profile_end waits for those events and writes one record per kernel
  * that ran (up to cap records to out; *count receives how many kernels
- * ran): launches (timed calls), the CUDA kernels those calls launched,
- * summed device time and two summed byte counts.  alg_bytes is the
+ * ran): launches (the library calls timed; the level steps of one
+ * level-wise build are timed together under one pair of events, so that no
+ * event separates them in the stream, and count one launch per level step),
+ * the CUDA kernels those calls launched, summed device time and two summed
+ * byte counts.  alg_bytes is the
  * level-wise method's byte model of the work the launch covers (per level:
  * symbols read, bitmap and directory written, next-level order written; a
  * step covering two levels counts both).  variant_bytes is what the

@@ -8,6 +8,7 @@
 #include <memory>
 #include <atomic>
 #include <mutex>
+#include <optional>
 #include <new>
 #include <vector>
 
@@ -89,6 +90,7 @@ struct ProfRecord {
     int kid;
     double bytes;    // the level-wise byte model of what the launch covers
     double vbytes;   // the bytes the launch's variant must move
+    uint64_t units;  // the launches (level steps) the record covers
     cudaEvent_t e0, e1;
     uint64_t k0, k1;  // kernel launch counter at the start and the end of the call
 };
@@ -117,16 +119,18 @@ struct Profiler {
 };
 Profiler g_prof;
 
-// Brackets one launch; a no-op when profiling is off.
+// Brackets one launch (or, with units = 0 and add(), several consecutive
+// launches of one kind, so that no event sits between them in the stream);
+// a no-op when profiling is off.
 struct ProfScope {
     int idx = -1;
     cudaStream_t st;
     unsigned flags = cudaEventRecordDefault;
     ProfScope(int kid, double bytes, cudaStream_t s) : ProfScope(kid, bytes, bytes, s) {}
-    ProfScope(int kid, double bytes, double vbytes, cudaStream_t s) : st(s) {
+    ProfScope(int kid, double bytes, double vbytes, cudaStream_t s, uint64_t units = 1) : st(s) {
         std::lock_guard<std::mutex> lk(g_prof.mu);
         if (!g_prof.on) return;
-        ProfRecord r{kid, bytes, vbytes, g_prof.take(), g_prof.take(), g_kernel_launches.load(), 0};
+        ProfRecord r{kid, bytes, vbytes, units, g_prof.take(), g_prof.take(), g_kernel_launches.load(), 0};
         if (!r.e0 || !r.e1) return;
         // Inside a stream capture the records become event nodes of the graph.
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -135,6 +139,14 @@ struct ProfScope {
         cudaEventRecordWithFlags(r.e0, st, flags);
         idx = (int)g_prof.recs.size();
         g_prof.recs.push_back(r);
+    }
+    // One more launch covered by this record.
+    void add(double bytes, double vbytes) {
+        if (idx < 0) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        g_prof.recs[idx].bytes += bytes;
+        g_prof.recs[idx].vbytes += vbytes;
+        g_prof.recs[idx].units++;
     }
     ~ProfScope() {
         if (idx < 0) return;
@@ -462,6 +474,12 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
         }
     }
     if (t->L > 0) {
+        // Without pair steps every level step is timed under one record, so
+        // no profiling event separates two level steps in the stream.
+        bool any_pair = false;
+        for (uint32_t l = 0; l < t->L; l++) any_pair = any_pair || pair[l];
+        std::optional<ProfScope> steps;
+        if (!any_pair) steps.emplace(K_LEVEL_PASS, 0.0, 0.0, st, 0);
         const void *cur = S;
         void *bufs[2] = {b.ping, b.pong};
         int bi = 0, pi = 0;
@@ -512,7 +530,11 @@ wt_status enqueue_levelwise(wt_tree *t, const void *S, cudaStream_t st, bool pai
                 const bool store = has_next && !(l + 2 == t->L && next_bits);
                 void *nxt = store ? bufs[bi] : nullptr;
                 const double vb = nw + t->n / 8.0 + t->n / 128.0 + (store ? nw : 0.0);
-                ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, has_next), vb, st);
+                std::optional<ProfScope> p;
+                if (any_pair)
+                    p.emplace(K_LEVEL_PASS, level_step_bytes(t->n, t->width, has_next), vb, st);
+                else
+                    steps->add(level_step_bytes(t->n, t->width, has_next), vb);
                 // Without a histogram: level l's tables and C_{l+1} from rank at C_l.
                 const RankTables rt{lv[l], sc.starts[l & 1], b.ob + ((1ull << l) - 1), b.ze + ((1ull << l) - 1),
                                     has_next ? sc.starts[(l + 1) & 1] : nullptr};
@@ -578,12 +600,13 @@ wt_status enqueue_matrix(wt_tree *t, const void *S, cudaStream_t st) {
         const void *cur = S;
         void *bufs[2] = {b.ping, b.pong};
         bool from_bits = false;
+        ProfScope steps(K_LEVEL_PASS, 0.0, 0.0, st, 0);  // every level step under one record
         for (uint32_t l = 0; l < t->L; l++) {
             const bool has_next = l + 1 < t->L;
             const bool next_bits = has_next && next0;
             const bool store = has_next && !(l + 2 == t->L && next_bits);
             void *nxt = store ? bufs[l & 1] : nullptr;
-            ProfScope p(K_LEVEL_PASS, level_step_bytes(t->n, t->width, has_next), st);
+            steps.add(level_step_bytes(t->n, t->width, has_next), level_step_bytes(t->n, t->width, has_next));
             WT_CK(launch_level_pass(cur, nxt, t->n, t->width, t->L, l, b.ob, b.ze, t->h_desc.lv[l],
                                     &t->d_desc->lv[l].ones, b.cnt, b.pre, from_bits,
                                     next_bits ? t->h_desc.lv[l + 1].words : nullptr, t->d_err, b.job_slot, st,
@@ -1755,7 +1778,7 @@ wt_status wt_profile_end(wt_kernel_stat_t *out, uint32_t cap, uint32_t *count) {
             r = WT_ERR_CUDA;
             continue;
         }
-        acc[rec.kid].launches++;
+        acc[rec.kid].launches += rec.units;
         acc[rec.kid].kernels += rec.k1 - rec.k0;
         acc[rec.kid].total_ms += ms;
         acc[rec.kid].alg_bytes += rec.bytes;

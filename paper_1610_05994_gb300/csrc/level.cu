@@ -55,6 +55,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "launch.cuh"
 #include "level_common.cuh"
 
 namespace wt {
@@ -241,6 +242,36 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(LevelLaunch a) {
     }
 }
 
+constexpr uint32_t kFoldNodes = 4096;
+
+// Level l's node tables by rank at the node boundaries C_l (the work of
+// rank_tables_kernel, which states the formulas), done by the last CTA of
+// the scan to finish: every CTA fences its directory writes and counts
+// itself done; the CTA that completes the count fences again and reads the
+// whole directory.  All threads of the CTA call this once.
+__device__ __forceinline__ void fold_rank_tables(const LevelLaunch &a) {
+    __shared__ uint32_t s_last;
+    if (!a.rt_nodes) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.rt_done, 1u) + 1 == gridDim.x * gridDim.y;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const LevelDesc lv = a.jobs[0].lv;
+    for (uint32_t v = threadIdx.x; v < a.rt_nodes; v += blockDim.x) {
+        const uint64_t c0 = a.rt_start_in[v], c1 = a.rt_start_in[v + 1];
+        const uint64_t r0 = rank1(lv, c0), r1 = rank1(lv, c1);
+        a.rt_ob[v] = r0;
+        a.rt_ze[v] = c1 - r1;
+        if (a.rt_start_out) {
+            a.rt_start_out[2 * v] = c0;
+            a.rt_start_out[2 * v + 1] = c1 - r1 + r0;
+            if (v + 1 == a.rt_nodes) a.rt_start_out[2 * a.rt_nodes] = c1;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     __shared__ uint64_t s_warp[32];
     __shared__ uint64_t s_base;
@@ -248,7 +279,10 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
     const LevelJob &J = a.jobs[job];
     const uint32_t nt = J.ntiles * a.units;  // units
-    if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) return;
+    if (seg * kScanSeg >= nt && !(seg == 0 && nt == 0)) {
+        fold_rank_tables(a);
+        return;
+    }
     const uint32_t way = blockIdx.y;
     if (way == 0 && seg == 0 && J.next_words && threadIdx.x < 32) {
         // Level l + 1's padding beyond n (the rest of its last 512-bit
@@ -365,6 +399,7 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
             *J.ones_out = total;
         }
     }
+    fold_rank_tables(a);
 }
 
 // ------------------------------------------------------------------ pass
@@ -939,12 +974,24 @@ static cudaError_t launch_lw(const LevelLaunch &a, bool from_bits, bool do_pass,
         note_launches(1);
         if (e != cudaSuccess) return e;
     }
+    // The level's node tables from its directory (no histogram): folded into
+    // the scan for few nodes, else their own launch after it.
+    LevelLaunch as = a;
+    const bool fold = rt && a.njobs == 1 && a.ways == 1 && (1ull << a.l) <= kFoldNodes;
+    if (fold) {
+        as.rt_nodes = 1u << a.l;
+        as.rt_done = const_cast<uint32_t *>(a.tile_start) + 2;
+        as.rt_start_in = rt->start_in;
+        as.rt_ob = rt->ob;
+        as.rt_ze = rt->ze;
+        as.rt_start_out = rt->start_out;
+    }
     const dim3 sg(a.njobs * a.segs, a.ways);
     cudaError_t e = launch_dependent(scan_sums_kernel, sg, 1024, 0, st, a);
-    if (e == cudaSuccess) e = launch_dependent(scan_segs_kernel, sg, 1024, 0, st, a);
+    if (e == cudaSuccess) e = launch_dependent(scan_segs_kernel, sg, 1024, 0, st, as);
     note_launches(2);
     if (e != cudaSuccess) return e;
-    if (rt) {  // the level's node tables from its directory (no histogram)
+    if (rt && !fold) {
         const cudaError_t e = launch_rank_tables(rt->lv, a.l, rt->start_in, rt->ob, rt->ze, rt->start_out, st);
         if (e != cudaSuccess) return e;
     }
@@ -1029,11 +1076,12 @@ __global__ void put_job_kernel(LevelJob j, LevelJob *dst, uint32_t *tile_start) 
     *dst = j;
     tile_start[0] = 0;
     tile_start[1] = j.ntiles;
+    tile_start[2] = 0;  // the scan's count of finished CTAs (fold_rank_tables)
 }
 
 size_t level_job_bytes() { return sizeof(LevelJob); }
 
-size_t level_job_slot_bytes() { return (sizeof(LevelJob) + 2 * sizeof(uint32_t) + 255) & ~size_t(255); }
+size_t level_job_slot_bytes() { return (sizeof(LevelJob) + 4 * sizeof(uint32_t) + 255) & ~size_t(255); }
 
 cudaError_t launch_level_count(const void *cur, uint64_t n, int width, uint32_t L, uint32_t l, LevelDesc lv,
                                uint32_t *cnt, uint32_t *next_words, uint32_t *err, void *job_slot, cudaStream_t st,

@@ -57,6 +57,13 @@ struct LevelLaunch {
     uint32_t ways;               // count arrays the scan turns into prefixes (1, or 3 for a pair step)
     uint32_t check_sigma;        // > 0: the count pass from the symbols flags any symbol >= check_sigma
     uint32_t one_node;           // every node has the same offsets: each tile is placed as node 0
+    // Level l's node tables folded into the scan (one job, at most
+    // kFoldNodes nodes): the last scan CTA to finish does rank_tables_kernel's
+    // work.  rt_nodes = 0: the tables come from their own launch, or none.
+    uint32_t rt_nodes;
+    uint32_t *rt_done;           // scan CTAs finished, zeroed by put_job_kernel
+    const uint64_t *rt_start_in;
+    uint64_t *rt_ob, *rt_ze, *rt_start_out;
 };
 
 // Whether some symbol of a 16-byte chunk is >= sigma (sigma >= 1).  For bytes

@@ -12,8 +12,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <utility>
-
 #include "../../include/wt.h"
 
 namespace wt {
@@ -159,32 +157,8 @@ __device__ __forceinline__ void fence_mbar_init() {
 // kernel has completed and its memory writes are visible.  Every kernel
 // launched this way calls griddep_wait before its first global-memory
 // access, so the stream's order of effects is unchanged.  (Outside such a
-// launch the instruction returns at once.)
+// launch the instruction returns at once.)  The host side is launch.cuh.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-// Launches kernel<<<grid, block, smem, st>>>(args...) with programmatic
-// stream serialization, except while st is being captured into a graph,
-// where it launches plainly.
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                                   Args &&...args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
-        cudaGetLastError();
-        cap = cudaStreamCaptureStatusActive;
-    }
-    cfg.attrs = attr;
-    cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
 
 // Orders this thread's earlier generic-proxy accesses to shared memory
 // before later async-proxy (bulk copy) writes.
