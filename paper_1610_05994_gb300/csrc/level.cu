@@ -274,6 +274,7 @@ __device__ __forceinline__ void fold_rank_tables(const LevelLaunch &a) {
 
 __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     __shared__ uint64_t s_warp[32];
+    __shared__ uint64_t s_bpart[32];
     __shared__ uint64_t s_base;
     griddep_wait();
     const uint32_t job = blockIdx.x / a.segs, seg = blockIdx.x % a.segs;
@@ -292,13 +293,11 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
     const uint32_t *cnt = J.cnt + way * way_cnt_stride(nt);
     uint64_t *pre = J.pre + way * way_pre_stride(nt);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (warp == 0) {
-        uint64_t b = 0;
-        for (uint32_t s2 = lane; s2 < seg; s2 += 32) b += pre[nt + 2 + s2];
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
-        if (lane == 0) s_base = b;
-    }
+    // The sums of the segments before this one: one load per thread per 1024
+    // segments, in flight with the count loads below and reduced beside the
+    // warp totals (no load waits on another).
+    uint64_t bsum = 0;
+    for (uint32_t s2 = tid; s2 < seg; s2 += 1024) bsum += pre[nt + 2 + s2];
     // kPer consecutive units per thread, read and written 16 bytes at a time
     // where the segment is whole.  A unit holds at most 512 ones, so the
     // sums of a thread, a warp and the CTA fit 32 bits.
@@ -328,7 +327,10 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
         if (lane >= d) inc += y;
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, d);
     if (lane == 31) s_warp[warp] = inc;
+    if (lane == 0) s_bpart[warp] = bsum;
     __syncthreads();
     if (warp == 0) {
         const uint32_t w = (uint32_t)s_warp[lane];
@@ -339,6 +341,10 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
             if (lane >= d) winc += y;
         }
         s_warp[lane] = winc - w;
+        uint64_t bb = s_bpart[lane];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, d);
+        if (lane == 0) s_base = bb;
     }
     __syncthreads();
     const uint64_t run0 = s_base + s_warp[warp] + (inc - sum);
@@ -377,8 +383,8 @@ __global__ void __launch_bounds__(1024) scan_segs_kernel(LevelLaunch a) {
 #pragma unroll
         for (int k = 0; k < kPer; k++) {
             const uint32_t t = t0 + k;
-            const uint64_t b = t / upb;
-            if (t < nt && t % upb == 0 && b < J.nblocks) {
+            const uint64_t b = upb == 1 ? t : t / upb;  // every unit is a rank block for all widths
+            if (t < nt && (upb == 1 || t % upb == 0) && b < J.nblocks) {
                 const uint64_t run = pv[k];
                 const uint64_t next = run + c[k] + (upb == 2 && k + 1 < kPer ? c[k + 1] : 0u);
                 if (!vec_r) J.lv.R[b] = (uint32_t)run;
